@@ -1,0 +1,74 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+``oracle.c`` compiled with ``-DORC_MUTANT=k`` plants one mistake (a wrong
+operand order, a flipped sign, a dropped term, a missing conjugate, a
+transposed operand, a wrong un-rotation sign, a wrong permutation order).  Each
+planted copy must fail at least one of the checks below, which use the same
+references as test_oracle_pins.py (closed forms, brute force, LAPACK on
+unique results).  Mistakes are planted only in the CPU oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import metrics
+from paper_2208_01239_gb300 import workloads as W
+
+MUTANTS = {
+    1: "X5 X2 instead of X2 X5 (Frobenius, explicit inverses)",
+    2: "X3 + iX4 instead of X3 - iX4 (Frobenius with LU)",
+    3: "X2 = B X1 instead of A + B X1 (Frobenius with LU)",
+    4: "missing conjugate in complex Cholesky",
+    5: "X1 X1^T instead of X1^T X1 (Frobenius with Cholesky)",
+    6: "X3 + mu X4 instead of X3 - mu X4 (almost sure un-rotation)",
+    7: "column swaps in forward order (left LU inverse)",
+}
+
+
+def _pin_failures(o) -> list:
+    fails = []
+    g = np.random.default_rng(9)
+    # brute force on small general matrices, every route
+    for n in (2, 3, 4):
+        m = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+        adj = o.adjugate_inv(m)
+        routes = {
+            "lu_left": lambda: o.cplx_lu_inv(m, left=True),
+            "lu_right": lambda: o.cplx_lu_inv(m, left=False),
+            "basic": lambda: o.frob_inv_basic(m),
+            "lu": lambda: o.frob_inv_lu(m),
+            "rand": lambda: o.frob_inv_rand(m, 0.37),
+        }
+        for name, f in routes.items():
+            try:
+                if metrics.forward_error(f(), adj) > 1e-12:
+                    fails.append(f"adjugate n={n} {name}")
+            except oracle.OracleError:
+                fails.append(f"adjugate n={n} {name} raised")
+    # LAPACK on a larger general matrix (more pivoting)
+    m = g.standard_normal((24, 24)) + 1j * g.standard_normal((24, 24))
+    ref = np.linalg.inv(m)
+    for left in (True, False):
+        if metrics.forward_error(o.cplx_lu_inv(m, left=left), ref) > 1e-10:
+            fails.append(f"lapack left={left}")
+    # HPD closed form, both Cholesky routes
+    ms, qs, lams = W.hpd(12, 1, seed=4, return_parts=True)
+    exact = W.hpd_exact_inverse(qs[0], lams[0])
+    for name, f in (("cplx_chol", o.cplx_chol_inv), ("frob_chol", o.frob_inv_chol)):
+        try:
+            if metrics.forward_error(f(ms[0]), exact) > 1e-9:
+                fails.append(f"hpd {name}")
+        except oracle.OracleError:
+            fails.append(f"hpd {name} raised")
+    return fails
+
+
+def test_clean_oracle_passes_the_pins(oracle_lib):
+    assert _pin_failures(oracle.load()) == []
+
+
+@pytest.mark.parametrize("k", sorted(MUTANTS), ids=lambda k: f"mutant{k}")
+def test_planted_mistake_is_caught(oracle_lib, k):
+    o = oracle.load(mutant=k)
+    fails = _pin_failures(o)
+    assert fails, f"planted mistake not caught: {MUTANTS[k]}"
