@@ -1,0 +1,169 @@
+/*
+ * frobinv.h -- C ABI of the GB300 (sm_103a) Frobenius inversion library.
+ *
+ * Frobenius inversion (Dai, Lim and Ye, "Complex matrix inversion via real
+ * matrix inversions", eq. (1.1) "Finv"): for M = A + iB with A, B real and A
+ * invertible,
+ *
+ *     M^{-1} = S^{-1} - i A^{-1} B S^{-1},   S = A + B A^{-1} B,
+ *
+ * so a complex inversion costs two real inversions, three real products and
+ * one real addition (Sec. 2, Algorithm "Frobenius inversion", tau = 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are square, complex and row-major, with the real and imaginary
+ *   parts interleaved: complex128 (two doubles) for FROB_FP64 and the mixed
+ *   modes, complex64 (two floats) for FROB_FP32.  Element (b, i, j) of a
+ *   strided batch lives at base + b * stride + i * ld + j (counted in complex
+ *   elements).  Because (M^T)^{-1} = (M^{-1})^T the row-major reading changes
+ *   nothing about the result.
+ * - All matrix pointers, the workspace and the info array are DEVICE
+ *   pointers owned by the caller.  The library never allocates: it runs in
+ *   the workspace of frob_workspace_bytes() bytes (256-byte aligned) that the
+ *   caller passes in.  Output and input must not overlap.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  Every call is asynchronous with respect to the host.
+ * - Host-visible argument errors (n < 1, batch < 1, ld < n, NULL pointers,
+ *   overlapping input/output, workspace too small, unsupported precision)
+ *   return synchronously and launch nothing.  FROB_ERR_CUDA means a launch
+ *   failed; the CUDA error is left for cudaGetLastError().
+ * - Numerical failures are per matrix and asynchronous: each matrix b gets a
+ *   frob_info record in info[b], written on the device.  status is a
+ *   frob_status and bad_index follows LAPACK's info convention (the 1-based
+ *   step whose pivot was exactly zero or not finite, or whose Cholesky
+ *   diagonal was not positive; n + j when the failure is in the second
+ *   factorisation, of S).  The entry point returns FROB_OK once the work has
+ *   been launched; read info after the stream has synchronised.
+ */
+#ifndef FROBINV_H
+#define FROBINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FROB_OK = 0,
+  FROB_ERR_ARG = 1,           /* bad argument (host, synchronous) */
+  FROB_ERR_SINGULAR = 2,      /* a pivot of A or S is exactly 0 or not finite */
+  FROB_ERR_NOT_HPD = 3,       /* a Cholesky diagonal of A or S is not positive */
+  FROB_ERR_NOT_CONVERGED = 4, /* refinement did not reach the tolerance */
+  FROB_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  FROB_ERR_CUDA = 6,          /* a CUDA launch failed */
+  FROB_ERR_WORKSPACE = 7,     /* workspace NULL, too small or misaligned */
+  FROB_ERR_UNSUPPORTED = 8    /* precision / operation not supported */
+} frob_status;
+
+typedef enum {
+  FROB_FP64 = 0,       /* complex128 in and out, FP64 arithmetic throughout */
+  FROB_FP32 = 1,       /* complex64 in and out, FP32 arithmetic throughout */
+  FROB_MIXED_TF32 = 2, /* complex128 in and out; TF32 tensor cores + refinement */
+  FROB_MIXED_BF16 = 3  /* complex128 in and out; BF16 tensor cores + refinement */
+} frob_prec;
+
+/* Operation codes for frob_workspace_bytes(). */
+typedef enum {
+  FROB_OP_INV = 0,       /* frob_inv */
+  FROB_OP_INV_HPD = 1,   /* frob_inv_hpd */
+  FROB_OP_CPLX_LU = 2,   /* cplx_lu_inv */
+  FROB_OP_CPLX_CHOL = 3  /* cplx_chol_inv */
+} frob_op;
+
+typedef struct {
+  int32_t prec;        /* frob_prec */
+  int32_t almost_sure; /* 1: Algorithm "Almost sure Frobenius inversion"
+                          (Sec. 4.2): invert (1 + mu i) M, then multiply the
+                          result by (1 + mu i).  Only for frob_inv. */
+  uint64_t seed;       /* mu for matrix b is a counter-based draw from
+                          (seed, b, attempt), uniform on (0, 1) */
+  int32_t attempt;     /* draw index; a caller that sees FROB_ERR_SINGULAR
+                          for matrix b may retry with attempt + 1 (Lemma
+                          "rand Frob": at most n values of mu fail) */
+  int32_t ns_max_iter; /* mixed modes: refinement iteration limit */
+  double ns_tol;       /* mixed modes: target ||I - M X||_F/(||M||_F ||X||_F) */
+} frob_opts;           /* NULL => {FROB_FP64, 0, 0, 0, 8, 1e-14} */
+
+typedef struct {
+  int32_t status;    /* frob_status of this matrix */
+  int32_t bad_index; /* LAPACK-style 1-based failing step, 0 if none */
+  int32_t ns_iters;  /* refinement iterations taken (mixed modes) */
+  int32_t fell_back; /* 1 if the mixed mode fell back to a wider format */
+  double mu;         /* the rotation used by the almost sure variant, else 0 */
+  double residual;   /* mixed modes: the last residual measured */
+} frob_info;         /* 32 bytes */
+
+/* Workspace size in bytes for `op` on `batch` matrices of order n in
+ * precision `prec`; 0 for invalid arguments. */
+size_t frob_workspace_bytes(int op, int n, int batch, int prec);
+
+/*
+ * frob_inv -- Frobenius inversion of a strided batch of general complex
+ * matrices (eq. (1.1); Algorithm "Frobenius inversion with LU decomposition",
+ * Sec. 4.1).  Per matrix: split M into planes A, B; LU with partial pivoting
+ * A = P1^T L1 U1; X1 = A^{-1} B by two triangular solves; S = A + B X1; LU of
+ * S; S^{-1} = U2^{-1} L2^{-1} P2; X = S^{-1} - i X1 S^{-1}, written
+ * interleaved.  With opts->almost_sure the input is first rotated,
+ * A' = A - mu B, B' = mu A + B, and the result un-rotated, X = (X3 - mu X4) +
+ * i (mu X3 + X4) (Sec. 4.2).  Fails per matrix with FROB_ERR_SINGULAR if A
+ * (bad_index = k) or S (bad_index = n + k) has an exactly zero pivot.
+ *
+ *   n, batch   order and number of matrices (n >= 1, batch >= 1)
+ *   M, ldm, sm input base, leading dimension (>= n), batch stride (elements)
+ *   X, ldx, sx output base, leading dimension, batch stride (elements)
+ *   opts       NULL or options (precision FROB_FP64 or FROB_FP32)
+ *   ws, wsb    device workspace and its size in bytes
+ *   info       device array of `batch` frob_info records (written)
+ */
+frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                     const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream);
+
+/*
+ * frob_inv_hpd -- Frobenius inversion of Hermitian positive definite
+ * matrices (Sec. 4.3, Algorithm "Frobenius inversion with Cholesky
+ * decomposition", and eq. (4.2) "cholesky").  Only the lower triangle of each
+ * M is read: A = Re (symmetric), B = Im (skew, zero diagonal).  Per matrix:
+ * A = R1^T R1; R1^T X1 = B; R1 X2 = X1; S = A - X1^T X1 (= A + B A^{-1} B);
+ * S = R2^T R2; R2^T X5 = I; R2 X6 = X5; X = X6 - i X2 X6, both triangles
+ * written.  Fails per matrix with FROB_ERR_NOT_HPD (bad_index = k for A,
+ * n + k for S).  Arguments as for frob_inv.
+ */
+frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                         const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream);
+
+/*
+ * cplx_lu_inv -- the baseline: inversion in complex arithmetic by LU with
+ * partial pivoting (Sec. 4, Algorithm "Inversion with LU decomposition"):
+ * M = P^T L U, then M^{-1} = U^{-1} L^{-1} P.  Arguments as for frob_inv;
+ * `prec` is FROB_FP64 (complex128) or FROB_FP32 (complex64).
+ */
+frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                        int prec, void* ws, size_t wsb, frob_info* info, void* stream);
+
+/*
+ * cplx_chol_inv -- the HPD baseline: inversion in complex arithmetic by
+ * Cholesky (Sec. 4.3, Algorithm "Inversion with Cholesky decomposition"):
+ * M = R^H R, R^H X1 = I, R X2 = X1, M^{-1} = X2.  Lower triangle read.
+ */
+frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
+                          int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* frob_status_str(int status);
+
+/* Library version string (static storage). */
+const char* frob_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads) since it was loaded.  Diagnostics: lets a caller count
+ * the kernels behind a call. */
+uint64_t frob_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FROBINV_H */

@@ -1,0 +1,189 @@
+// C-ABI entry points of libfrobinv (declared in include/frobinv.h): argument
+// checks, workspace sizing and dispatch to the per-precision drivers.
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "../../include/frobinv.h"
+#include "common.cuh"
+#include "ops.h"
+
+using namespace frob;
+
+namespace frob {
+static std::atomic<uint64_t> g_launches{0};
+static int debug_level() {
+  static int level = [] {
+    const char* e = std::getenv("FROB_DEBUG_SYNC");
+    return e ? std::atoi(e) : 0;
+  }();
+  return level;
+}
+void launch_begin(const char* name) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (debug_level()) {
+    std::fprintf(stderr, "[frob] launch %s\n", name);
+    std::fflush(stderr);
+  }
+}
+void launch_end(const char* name, cudaStream_t st) {
+  if (debug_level()) {
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    std::fprintf(stderr, "[frob] done %s: launch=%s sync=%s\n", name, cudaGetErrorString(e1), cudaGetErrorString(e2));
+    std::fflush(stderr);
+  }
+}
+}  // namespace frob
+
+namespace {
+
+frob_opts default_opts() {
+  frob_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.prec = FROB_FP64;
+  o.ns_max_iter = 8;
+  o.ns_tol = 1e-14;
+  return o;
+}
+
+bool valid_prec(int p) { return p == FROB_FP64 || p == FROB_FP32; }
+
+size_t elem_bytes(int prec) { return prec == FROB_FP32 ? 8 : 16; }
+
+// Overlap test of the byte ranges touched by two strided batches.
+bool overlaps(const void* a, int64_t lda, int64_t sa, const void* b, int64_t ldb, int64_t sb, int n, int batch,
+              size_t eb) {
+  auto span = [&](int64_t ld, int64_t s) {
+    return (size_t)(((int64_t)(batch - 1) * s + (int64_t)(n - 1) * ld + n) * (int64_t)eb);
+  };
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  size_t la = span(lda, sa), lb = span(ldb, sb);
+  return pa < pb + lb && pb < pa + la;
+}
+
+frob_status check_common(int n, int batch, const void* M, int64_t ldm, int64_t sm, const void* X, int64_t ldx,
+                         int64_t sx, void* ws, size_t wsb, size_t need, frob_info* info, int prec) {
+  if (n < 1 || batch < 1 || batch > 65535) return FROB_ERR_ARG;
+  if (!M || !X || !info) return FROB_ERR_ARG;
+  if (ldm < n || ldx < n) return FROB_ERR_ARG;
+  if (batch > 1 && (sm < ldm * (int64_t)n || sx < ldx * (int64_t)n)) return FROB_ERR_ARG;
+  if (overlaps(M, ldm, sm, X, ldx, sx, n, batch, elem_bytes(prec))) return FROB_ERR_ARG;
+  if (!valid_prec(prec)) return FROB_ERR_UNSUPPORTED;
+  if (!ws || wsb < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return FROB_ERR_WORKSPACE;
+  return FROB_OK;
+}
+
+frob_status launched() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;
+}
+
+template <typename T> MatB<const T> in_view(const void* p, int64_t ld, int64_t s) {
+  return MatB<const T>{static_cast<const T*>(p), ld, s};
+}
+template <typename T> MatB<T> out_view(void* p, int64_t ld, int64_t s) {
+  return MatB<T>{static_cast<T*>(p), ld, s};
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
+  if (n < 1 || batch < 1 || !valid_prec(prec)) return 0;
+  const bool f32 = prec == FROB_FP32;
+  switch (op) {
+    case FROB_OP_INV:
+      return f32 ? frob_lu_ws<float>(n, batch, nullptr, nullptr) : frob_lu_ws<double>(n, batch, nullptr, nullptr);
+    case FROB_OP_INV_HPD:
+      return f32 ? frob_chol_ws<float>(n, batch, nullptr, nullptr) : frob_chol_ws<double>(n, batch, nullptr, nullptr);
+    case FROB_OP_CPLX_LU:
+      return f32 ? cplx_lu_ws<zf>(n, batch, nullptr, nullptr) : cplx_lu_ws<zd>(n, batch, nullptr, nullptr);
+    case FROB_OP_CPLX_CHOL:
+      return f32 ? cplx_chol_ws<zf>(n, batch, nullptr, nullptr) : cplx_chol_ws<zd>(n, batch, nullptr, nullptr);
+    default:
+      return 0;
+  }
+}
+
+frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                     const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
+  frob_opts o = opts ? *opts : default_opts();
+  if (o.almost_sure != 0 && o.almost_sure != 1) return FROB_ERR_ARG;
+  frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
+                               frob_workspace_bytes(FROB_OP_INV, n, batch, o.prec), info, o.prec);
+  if (s != FROB_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.prec == FROB_FP32)
+    frob_lu_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), o, ws, info, st);
+  else
+    frob_lu_run<double>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st);
+  return launched();
+}
+
+frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                         const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
+  frob_opts o = opts ? *opts : default_opts();
+  if (o.almost_sure) return FROB_ERR_ARG;  // A is SPD for HPD input (Lemma "positive real part")
+  frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
+                               frob_workspace_bytes(FROB_OP_INV_HPD, n, batch, o.prec), info, o.prec);
+  if (s != FROB_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.prec == FROB_FP32)
+    frob_chol_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
+  else
+    frob_chol_run<double>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  return launched();
+}
+
+frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
+                        int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
+  frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
+                               frob_workspace_bytes(FROB_OP_CPLX_LU, n, batch, prec), info, prec);
+  if (s != FROB_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == FROB_FP32)
+    cplx_lu_run<zf>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
+  else
+    cplx_lu_run<zd>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  return launched();
+}
+
+frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
+                          int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
+  frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
+                               frob_workspace_bytes(FROB_OP_CPLX_CHOL, n, batch, prec), info, prec);
+  if (s != FROB_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == FROB_FP32)
+    cplx_chol_run<zf>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
+  else
+    cplx_chol_run<zd>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  return launched();
+}
+
+const char* frob_status_str(int status) {
+  switch (status) {
+    case FROB_OK: return "FROB_OK";
+    case FROB_ERR_ARG: return "FROB_ERR_ARG";
+    case FROB_ERR_SINGULAR: return "FROB_ERR_SINGULAR";
+    case FROB_ERR_NOT_HPD: return "FROB_ERR_NOT_HPD";
+    case FROB_ERR_NOT_CONVERGED: return "FROB_ERR_NOT_CONVERGED";
+    case FROB_ERR_TIMEOUT: return "FROB_ERR_TIMEOUT";
+    case FROB_ERR_CUDA: return "FROB_ERR_CUDA";
+    case FROB_ERR_WORKSPACE: return "FROB_ERR_WORKSPACE";
+    case FROB_ERR_UNSUPPORTED: return "FROB_ERR_UNSUPPORTED";
+    default: return "FROB_ERR_UNKNOWN";
+  }
+}
+
+const char* frob_version(void) { return "frobinv 0.1 sm_103a"; }
+
+uint64_t frob_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,551 @@
+// Dense building blocks of Frobenius inversion on the CUDA cores (FP64 DFMA /
+// FP32 FFMA), templated over the scalar type:
+//   T = double, float  -> the real planes of Frobenius inversion (Sec. 4.1,
+//                         4.3 of Dai, Lim and Ye)
+//   T = zd, zf         -> complex arithmetic for the baselines
+//                         (Algorithms "Inversion with LU / Cholesky
+//                         decomposition")
+//
+// On GB300 the FP64 pipe retires about 2 DFMA per clock per SM, so every FP64
+// kernel here is bound by that pipe, not by memory: the design goal is to keep
+// all 152 SMs issuing FMAs (batched grids over tiles x matrices), not to
+// minimise bytes.
+//
+// Kernels:
+//   gemm_kernel        D = alpha op(A) op(B) + beta C, 64x64 tiles, with a
+//                      pluggable epilogue (plain, or the Frobenius output
+//                      writer that interleaves Re/Im, permutes columns and
+//                      applies the almost-sure un-rotation).
+//   trsm_step_kernel   one block row of a blocked triangular solve
+//                      op(T) X = B: a GEMM over the finished block rows, then
+//                      substitution with the 64x64 diagonal block in shared
+//                      memory.  Optionally B = I with the zero blocks of the
+//                      triangular result skipped.
+//   getrf_panel_kernel LU with partial pivoting of one column panel; pivot
+//                      search by warp-shuffle argmax.
+//   laswp_trsm_kernel  applies a panel's row swaps to the other columns and
+//                      forms U12 = L11^{-1} A12.
+//   potrf_panel_kernel Cholesky of one column panel (lower, A = L L^H).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "ops.h"
+
+namespace frob {
+
+constexpr int TB = 64;   // tile rows / cols (also the block size of the blocked solvers)
+constexpr int TK = 16;   // k step of the GEMM mainloop
+constexpr int NTH = 256; // threads per GEMM / TRSM CTA
+
+// ------------------------------------------------------------------ mainloop
+// acc[r][c] += sum_{k in [kbeg, kend)} opA(i0 + ty + 16 r, k) * opB(k, j0 + tx + 16 c)
+// where opA(i, k) = A[i][k] (OP_N), A[k][i] (OP_T) or conj(A[k][i]) (OP_C),
+// and opB(k, j) = B[k][j] (OP_N), B[j][k] (OP_T) or conj(B[j][k]) (OP_C).
+// Out-of-range rows (>= M), columns (>= N) and k (>= kend) read as zero.
+template <typename T> struct SmemAB {
+  T a[TK][TB + 1];
+  T b[TK][TB + 1];
+};
+
+template <typename T, int OPA>
+__device__ __forceinline__ T load_opA(const T* A, int64_t lda, int i, int k, int M, int kend) {
+  if (i >= M || k >= kend) return zero_v<T>();
+  if (OPA == OP_N) return A[(int64_t)i * lda + k];
+  T v = A[(int64_t)k * lda + i];
+  return OPA == OP_C ? conj_(v) : v;
+}
+template <typename T, int OPB>
+__device__ __forceinline__ T load_opB(const T* B, int64_t ldb, int k, int j, int N, int kend) {
+  if (j >= N || k >= kend) return zero_v<T>();
+  if (OPB == OP_N) return B[(int64_t)k * ldb + j];
+  T v = B[(int64_t)j * ldb + k];
+  return OPB == OP_C ? conj_(v) : v;
+}
+
+template <typename T, int OPA, int OPB>
+__device__ __forceinline__ void mainloop(T (&acc)[4][4], SmemAB<T>& sm, const T* A, int64_t lda, const T* B,
+                                         int64_t ldb, int M, int N, int i0, int j0, int kbeg, int kend) {
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  T ra[4], rb[4];
+  // element e = t + 256 q of the 64x16 A tile / 16x64 B tile; the mapping
+  // keeps consecutive threads on consecutive addresses of the source.
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = t + NTH * q;
+      int il, kl;
+      if (OPA == OP_N) { il = e >> 4; kl = e & 15; } else { il = e & 63; kl = e >> 6; }
+      ra[q] = load_opA<T, OPA>(A, lda, i0 + il, k0 + kl, M, kend);
+      int jl, kl2;
+      if (OPB == OP_N) { jl = e & 63; kl2 = e >> 6; } else { jl = e >> 4; kl2 = e & 15; }
+      rb[q] = load_opB<T, OPB>(B, ldb, k0 + kl2, j0 + jl, N, kend);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = t + NTH * q;
+      int il, kl;
+      if (OPA == OP_N) { il = e >> 4; kl = e & 15; } else { il = e & 63; kl = e >> 6; }
+      sm.a[kl][il] = ra[q];
+      int jl, kl2;
+      if (OPB == OP_N) { jl = e & 63; kl2 = e >> 6; } else { jl = e >> 4; kl2 = e & 15; }
+      sm.b[kl2][jl] = rb[q];
+    }
+  };
+  if (kbeg >= kend) return;
+  fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += TK) {
+    __syncthreads();
+    stash();
+    __syncthreads();
+    if (k0 + TK < kend) fetch(k0 + TK);
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = sm.a[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = sm.b[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mac(acc[r][c], av[r], bv[c]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ GEMM
+// Epilogue: D = alpha * acc + beta * C (C may alias D; C is not read when
+// beta_is_zero).
+template <typename T> struct EpiAxpby {
+  MatB<T> D;
+  MatB<const T> C;
+  T alpha, beta;
+  int beta_is_zero;
+  __device__ __forceinline__ void operator()(int b, int i, int j, T v) const {
+    T out = mul_(alpha, v);
+    if (!beta_is_zero) out = add_(out, mul_(beta, C.at(b)[(int64_t)i * C.ld + j]));
+    D.at(b)[(int64_t)i * D.ld + j] = out;
+  }
+};
+
+// The last product of Frobenius inversion, W = X1 Z with Z = S^{-1} (up to
+// the column permutation P2), written straight into the interleaved complex
+// result (Sec. 4.1, Algorithm "Frobenius inversion with LU decomposition",
+// output X3 - i X4 with X3 = S^{-1}, X4 = X1 S^{-1}):
+//   X[i][dst(j)] = (Z[i][j], -W[i][j])                         (mu = 0)
+//   X[i][dst(j)] = (X3 - mu X4, mu X3 + X4), X3 = Z, X4 = -W   (almost sure,
+//                                                  Sec. 4.2, Algorithm "Almost
+//                                                  sure Frobenius inversion")
+// dst = rowperm of P2 (S^{-1} = Z P2 moves column j of Z to column rp[j]);
+// NULL for no permutation (Cholesky variant).
+template <typename R> struct EpiFrobOut {
+  using C = typename cplx_of<R>::type;
+  MatB<C> X;
+  MatB<const R> Z;
+  const int* rp;     // per-matrix permutation, batch stride n, or NULL
+  int n;
+  const frob_info* info; // info[b].mu, or NULL for mu = 0
+  __device__ __forceinline__ void operator()(int b, int i, int j, R w) const {
+    R x3 = Z.at(b)[(int64_t)i * Z.ld + j];
+    R x4 = -w;
+    int jd = rp ? rp[(int64_t)b * n + j] : j;
+    C out;
+    if (info) {
+      R mu = (R)info[b].mu;
+      out.x = x3 - mu * x4;
+      out.y = mu * x3 + x4;
+    } else {
+      out.x = x3;
+      out.y = x4;
+    }
+    X.at(b)[(int64_t)i * X.ld + jd] = out;
+  }
+};
+
+// tile_mode: 0 = all tiles; 1 = only tiles that touch the lower triangle
+// (j0 <= i0 + 63), for products known to be symmetric / Hermitian.
+template <typename T, int OPA, int OPB, class Epi>
+__global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<const T> A, MatB<const T> B, Epi epi,
+                                                   int tile_mode) {
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * TB, j0 = blockIdx.x * TB;
+  if (tile_mode == 1 && j0 > i0 + TB - 1) return;
+  __shared__ SmemAB<T> sm;
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = zero_v<T>();
+  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, 0, K);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+      if (i < M && j < N) epi(b, i, j, acc[r][c]);
+    }
+}
+
+// ------------------------------------------------------------------ TRSM step
+// Block row kb (rows [kb*64, kb*64+64)) of op(T) X = B for one 64-column tile
+// of X per CTA (grid: column tiles x batch).
+//   LOWER: op(T) is lower triangular -> uses the finished block rows j < kb
+//          (forward substitution); else upper -> j > kb (backward).
+//   UNIT:  unit diagonal (the L of an LU factorisation).
+//   RHS_I: B = I restricted to the tile; tiles right of the diagonal block
+//          are zero and are written as such (the inverse of a lower
+//          triangular matrix is lower triangular), and the sum skips the
+//          block rows j < column tile where X is zero.
+//   rowperm (optional): B row r is read from row rowperm[r] (B := P B).
+// X may alias B when rowperm is NULL.
+template <typename T> struct SmemTrsm {
+  union {
+    SmemAB<T> ab;
+    T d[TB][TB + 1];
+  } u;
+  T w[TB][TB + 1];
+  T dinv[TB];
+};
+
+template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
+__global__ void __launch_bounds__(NTH) trsm_step_kernel(int n, int nrhs, int kb, MatB<const T> Tm, MatB<const T> Bm,
+                                                        MatB<T> X, const int* rowperm) {
+  const int b = blockIdx.z;
+  const int ct = blockIdx.x;
+  const int c0 = ct * TB;
+  const int r0 = kb * TB;
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SmemTrsm<T>& sm = *reinterpret_cast<SmemTrsm<T>*>(smraw);
+  T* Xb = X.at(b);
+  const T* Tb = Tm.at(b);
+
+  if (RHS_I && LOWER && ct > kb) {
+    for (int e = t; e < TB * TB; e += NTH) {
+      int r = r0 + e / TB, c = c0 + e % TB;
+      if (r < n && c < nrhs) Xb[(int64_t)r * X.ld + c] = zero_v<T>();
+    }
+    return;
+  }
+
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = zero_v<T>();
+
+  // acc = sum_j op(T)[r0.., j] X[j, c0..]  over the finished rows
+  {
+    int kbeg, kend;
+    if (LOWER) { kbeg = RHS_I ? c0 : 0; kend = r0; }
+    else { kbeg = r0 + TB; kend = n; }
+    if (kbeg < kend) {
+      // op(T) restricted to rows [r0, r0+64): pass the row offset through the pointer
+      const T* Tp;
+      if (OPT == OP_N) Tp = Tb + (int64_t)r0 * Tm.ld; else Tp = Tb + r0;
+      mainloop<T, OPT, OP_N>(acc, sm.u.ab, Tp, Tm.ld, Xb, X.ld, n - r0, nrhs, 0, c0, kbeg, kend);
+    }
+  }
+  __syncthreads();
+  // w = B_tile - acc
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int rl = ty + 16 * r, cl = tx + 16 * c;
+      int gr = r0 + rl, gc = c0 + cl;
+      T bv = zero_v<T>();
+      if (gr < n && gc < nrhs) {
+        if (RHS_I) bv = (gr == gc) ? one_v<T>() : zero_v<T>();
+        else {
+          int sr = rowperm ? rowperm[(int64_t)b * n + gr] : gr;
+          bv = Bm.at(b)[(int64_t)sr * Bm.ld + gc];
+        }
+      }
+      sm.w[rl][cl] = sub_(bv, acc[r][c]);
+    }
+  // diagonal block op(T)[r0.., r0..], masked to its triangle; padding rows
+  // beyond n act as identity rows
+  for (int e = t; e < TB * TB; e += NTH) {
+    int rl = e / TB, cl = e % TB;
+    int gr = r0 + rl, gc = r0 + cl;
+    T v = zero_v<T>();
+    bool in_tri = LOWER ? (cl <= rl) : (cl >= rl);
+    if (gr < n && gc < n && in_tri) {
+      if (OPT == OP_N) v = Tb[(int64_t)gr * Tm.ld + gc];
+      else {
+        v = Tb[(int64_t)gc * Tm.ld + gr];
+        if (OPT == OP_C) v = conj_(v);
+      }
+    }
+    if (rl == cl && (UNIT || gr >= n)) v = one_v<T>();
+    sm.u.d[rl][cl] = v;
+  }
+  __syncthreads();
+  if (t < TB) sm.dinv[t] = UNIT ? one_v<T>() : recip_(sm.u.d[t][t]);
+  __syncthreads();
+  // substitution: 4 lanes per column (same warp), 64 columns
+  {
+    const int col = t >> 2, part = t & 3;
+    const unsigned mask = 0xffffffffu;
+    for (int s = 0; s < TB; ++s) {
+      int rr = LOWER ? s : (TB - 1 - s);
+      T p = zero_v<T>();
+      if (LOWER) {
+        for (int l = part; l < rr; l += 4) mac(p, sm.u.d[rr][l], sm.w[l][col]);
+      } else {
+        for (int l = rr + 1 + part; l < TB; l += 4) mac(p, sm.u.d[rr][l], sm.w[l][col]);
+      }
+      // reduce over the 4 lanes of this column
+      if constexpr (is_cplx<T>::value) {
+        p.x += __shfl_xor_sync(mask, p.x, 1);
+        p.y += __shfl_xor_sync(mask, p.y, 1);
+        p.x += __shfl_xor_sync(mask, p.x, 2);
+        p.y += __shfl_xor_sync(mask, p.y, 2);
+      } else {
+        p += __shfl_xor_sync(mask, p, 1);
+        p += __shfl_xor_sync(mask, p, 2);
+      }
+      if (part == 0) sm.w[rr][col] = mul_(sub_(sm.w[rr][col], p), sm.dinv[rr]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < TB * TB; e += NTH) {
+    int rl = e / TB, cl = e % TB;
+    int gr = r0 + rl, gc = c0 + cl;
+    if (gr < n && gc < nrhs) Xb[(int64_t)gr * X.ld + gc] = sm.w[rl][cl];
+  }
+}
+
+// ------------------------------------------------------------------ panels
+// Pivot key: |x| for reals, |re|^2 + |im|^2 for complex numbers (both give
+// the entry of largest modulus).
+__device__ __forceinline__ double pkey(double a) { return fabs(a); }
+__device__ __forceinline__ float pkey(float a) { return fabsf(a); }
+__device__ __forceinline__ double pkey(zd a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float pkey(zf a) { return a.x * a.x + a.y * a.y; }
+
+template <typename K> struct KeyIdx {
+  K key;
+  int idx;
+};
+
+// larger key wins; equal keys -> lower index; NaN keys never win
+template <typename K> __device__ __forceinline__ KeyIdx<K> kmax(KeyIdx<K> a, KeyIdx<K> b) {
+  if (b.key > a.key || (b.key == a.key && b.idx < a.idx)) return b;
+  return a;
+}
+
+constexpr int PANEL_THREADS = 512;
+
+// LU with partial pivoting of the column panel [k0, k0+kb) over rows [k0, n)
+// of each matrix (grid: batch).  The panel is staged in shared memory when
+// `staged` (rows * kb * sizeof(T) fits), else factored in place in global
+// memory.  piv[k] (absolute row, batch stride n) receives the row exchanged
+// with row k.  A zero or non-finite pivot reports FROB_ERR_SINGULAR with
+// bad_index = k + 1 + info_off and leaves that column unscaled.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS) getrf_panel_kernel(int n, int k0, int kb, MatB<T> A, int* piv,
+                                                                     frob_info* info, int info_off, int staged) {
+  using K = typename real_of<T>::type;
+  const int b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int m = n - k0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ KeyIdx<K> red[PANEL_THREADS / 32];
+  __shared__ int s_p;
+  __shared__ T s_rinv;
+  __shared__ int s_ok;
+  T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
+  T* P;
+  int64_t ps;
+  if (staged) {
+    P = reinterpret_cast<T*>(smraw);
+    ps = kb;
+    for (int e = t; e < m * kb; e += PANEL_THREADS) P[e] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
+    __syncthreads();
+  } else {
+    P = g;
+    ps = A.ld;
+  }
+  for (int j = 0; j < kb; ++j) {
+    // argmax over rows [j, m) of column j
+    KeyIdx<K> best{(K)-1, 0x7fffffff};
+    bool bad = false;
+    for (int r = j + t; r < m; r += PANEL_THREADS) {
+      K kv = pkey(P[(int64_t)r * ps + j]);
+      if (!(kv == kv) || kv == (K)INFINITY) bad = true;
+      best = kmax(best, KeyIdx<K>{kv, r});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, best.key, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+      best = kmax(best, other);
+    }
+    bad = __syncthreads_or(bad);
+    if ((t & 31) == 0) red[t >> 5] = best;
+    __syncthreads();
+    if (t == 0) {
+      KeyIdx<K> bb = red[0];
+      for (int w = 1; w < PANEL_THREADS / 32; ++w) bb = kmax(bb, red[w]);
+      int p = (bb.idx == 0x7fffffff) ? j : bb.idx;
+      s_p = p;
+      piv[(int64_t)b * n + k0 + j] = k0 + p;
+      T pv = P[(int64_t)p * ps + j];
+      bool ok = !bad && bb.key > (K)0;
+      s_ok = ok;
+      if (!ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+      s_rinv = ok ? recip_(pv) : one_v<T>();
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)
+      for (int c = t; c < kb; c += PANEL_THREADS) {
+        T x = P[(int64_t)j * ps + c];
+        P[(int64_t)j * ps + c] = P[(int64_t)p * ps + c];
+        P[(int64_t)p * ps + c] = x;
+      }
+    __syncthreads();
+    if (s_ok) {
+      const T rinv = s_rinv;
+      for (int r = j + 1 + t; r < m; r += PANEL_THREADS) P[(int64_t)r * ps + j] = mul_(P[(int64_t)r * ps + j], rinv);
+    }
+    __syncthreads();
+    // rank-1 update of the rest of the panel
+    for (int r = j + 1 + t; r < m; r += PANEL_THREADS) {
+      T l = neg_(P[(int64_t)r * ps + j]);
+      T* row = P + (int64_t)r * ps;
+      const T* prow = P + (int64_t)j * ps;
+      for (int c = j + 1; c < kb; ++c) mac(row[c], l, prow[c]);
+    }
+    __syncthreads();
+  }
+  if (staged) {
+    for (int e = t; e < m * kb; e += PANEL_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[e];
+  }
+}
+
+// Row swaps of the panel [k0, k0+kb) applied to the columns outside it, and
+// U12 = L11^{-1} A12 for the columns right of it (grid: column strips of 64
+// x batch).  Strip s covers columns [64 s, 64 s + 64) of the matrix; columns
+// inside the panel are skipped.
+constexpr int PANEL_MAX = 32;  // widest column panel of the blocked LU / Cholesky
+
+template <typename T> constexpr size_t laswp_trsm_smem() {
+  return sizeof(T) * (size_t)(PANEL_MAX * (PANEL_MAX + 1) + PANEL_MAX * (TB + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, MatB<T> A, const int* piv) {
+  const int b = blockIdx.z;
+  const int t = threadIdx.x;
+  const int c0 = blockIdx.x * TB;
+  T* Ab = A.at(b);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* l11 = reinterpret_cast<T*>(smraw);              // [kb][PANEL_MAX + 1]
+  T* u = l11 + PANEL_MAX * (PANEL_MAX + 1);          // [kb][TB + 1]
+  constexpr int LS = PANEL_MAX + 1, US = TB + 1;
+  const int c = c0 + (t & 63);
+  const bool col_ok = c < n && (c < k0 || c >= k0 + kb);
+  // swaps, in order
+  if (t < TB && col_ok) {
+    for (int j = 0; j < kb; ++j) {
+      int p = piv[(int64_t)b * n + k0 + j];
+      if (p != k0 + j) {
+        T x = Ab[(int64_t)(k0 + j) * A.ld + c];
+        Ab[(int64_t)(k0 + j) * A.ld + c] = Ab[(int64_t)p * A.ld + c];
+        Ab[(int64_t)p * A.ld + c] = x;
+      }
+    }
+  }
+  if (c0 + TB <= k0 + kb) return;  // strip entirely left of / inside the panel
+  __syncthreads();
+  for (int e = t; e < kb * kb; e += NTH) {
+    int r = e / kb, q = e % kb;
+    l11[r * LS + q] = Ab[(int64_t)(k0 + r) * A.ld + k0 + q];
+  }
+  for (int e = t; e < kb * TB; e += NTH) {
+    int r = e / TB, q = e % TB;
+    int cc = c0 + q;
+    u[r * US + q] = (cc < n && cc >= k0 + kb) ? Ab[(int64_t)(k0 + r) * A.ld + cc] : zero_v<T>();
+  }
+  __syncthreads();
+  // forward substitution with the unit lower triangle L11, one column per thread
+  if (t < TB) {
+    for (int r = 1; r < kb; ++r) {
+      T s = u[r * US + t];
+      for (int q = 0; q < r; ++q) mac(s, neg_(l11[r * LS + q]), u[q * US + t]);
+      u[r * US + t] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < kb * TB; e += NTH) {
+    int r = e / TB, q = e % TB;
+    int cc = c0 + q;
+    if (cc < n && cc >= k0 + kb) Ab[(int64_t)(k0 + r) * A.ld + cc] = u[r * US + q];
+  }
+}
+
+// Cholesky A = L L^H of the column panel [k0, k0+kb) over rows [k0, n),
+// lower triangle (grid: batch).  A non-positive or non-finite diagonal
+// reports FROB_ERR_NOT_HPD with bad_index = k + 1 + info_off.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS) potrf_panel_kernel(int n, int k0, int kb, MatB<T> A,
+                                                                     frob_info* info, int info_off, int staged) {
+  using K = typename real_of<T>::type;
+  const int b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int m = n - k0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ K s_rinv;
+  T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
+  T* P;
+  int64_t ps;
+  if (staged) {
+    P = reinterpret_cast<T*>(smraw);
+    ps = kb;
+    for (int e = t; e < m * kb; e += PANEL_THREADS) P[e] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
+    __syncthreads();
+  } else {
+    P = g;
+    ps = A.ld;
+  }
+  for (int j = 0; j < kb; ++j) {
+    if (t == 0) {
+      K d = real_(P[(int64_t)j * ps + j]);
+      bool ok = d > (K)0 && d < (K)INFINITY;
+      if (!ok) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + j + 1);
+      K l = ok ? sqrt(d) : (K)1;
+      P[(int64_t)j * ps + j] = from_real<T>(l);
+      s_rinv = (K)1 / l;
+    }
+    __syncthreads();
+    const K rinv = s_rinv;
+    for (int r = j + 1 + t; r < m; r += PANEL_THREADS) {
+      T v = P[(int64_t)r * ps + j];
+      P[(int64_t)r * ps + j] = mul_(v, from_real<T>(rinv));
+    }
+    __syncthreads();
+    for (int r = j + 1 + t; r < m; r += PANEL_THREADS) {
+      T l = neg_(P[(int64_t)r * ps + j]);
+      T* row = P + (int64_t)r * ps;
+      int cmax = r < kb - 1 ? r : kb - 1;
+      for (int c = j + 1; c <= cmax; ++c) mac(row[c], l, conj_(P[(int64_t)c * ps + j]));
+    }
+    __syncthreads();
+  }
+  if (staged) {
+    for (int e = t; e < m * kb; e += PANEL_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[e];
+  }
+}
+
+}  // namespace frob

@@ -1,0 +1,9 @@
+// Explicit instantiation of the inversion drivers for float / zf.
+#include "ops_impl.cuh"
+
+namespace frob {
+template size_t frob_lu_ws<float>(int, int, void*, Planes<float>*);
+template void frob_lu_run<float>(int, int, MatB<const zf>, MatB<zf>, const frob_opts&, void*, frob_info*, cudaStream_t);
+template size_t frob_chol_ws<float>(int, int, void*, Planes<float>*);
+template void frob_chol_run<float>(int, int, MatB<const zf>, MatB<zf>, void*, frob_info*, cudaStream_t);
+}  // namespace frob

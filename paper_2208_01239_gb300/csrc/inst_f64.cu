@@ -1,0 +1,9 @@
+// Explicit instantiation of the inversion drivers for double / zd.
+#include "ops_impl.cuh"
+
+namespace frob {
+template size_t frob_lu_ws<double>(int, int, void*, Planes<double>*);
+template void frob_lu_run<double>(int, int, MatB<const zd>, MatB<zd>, const frob_opts&, void*, frob_info*, cudaStream_t);
+template size_t frob_chol_ws<double>(int, int, void*, Planes<double>*);
+template void frob_chol_run<double>(int, int, MatB<const zd>, MatB<zd>, void*, frob_info*, cudaStream_t);
+}  // namespace frob

@@ -1,0 +1,42 @@
+// Declarations shared between the per-precision instantiation units and the
+// C-ABI entry points.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace frob {
+
+template <typename R> struct cplx_of;
+template <> struct cplx_of<double> { using type = zd; };
+template <> struct cplx_of<float> { using type = zf; };
+
+// Workspace planes of the Frobenius routines (real, n x n per matrix).
+template <typename R> struct Planes {
+  MatB<R> LA, S, Bp, X1, Y;
+  int *piv1, *piv2, *rp1, *rp2;
+};
+// Workspace of the complex baselines.
+template <typename C> struct CPlanes {
+  MatB<C> W, Y;
+  int *piv, *rp;
+};
+
+template <typename R> size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out);
+template <typename R>
+void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
+                 const frob_opts& o, void* ws, frob_info* info, cudaStream_t st);
+template <typename R> size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out);
+template <typename R>
+void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
+                   void* ws, frob_info* info, cudaStream_t st);
+template <typename C> size_t cplx_lu_ws(int n, int batch, void* ws, CPlanes<C>* out);
+template <typename C> void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info,
+                                       cudaStream_t st);
+template <typename C> size_t cplx_chol_ws(int n, int batch, void* ws, CPlanes<C>* out);
+template <typename C> void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info,
+                                         cudaStream_t st);
+
+}  // namespace frob

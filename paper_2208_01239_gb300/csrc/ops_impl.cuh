@@ -1,0 +1,370 @@
+// Host-side drivers: the blocked factorisations and solves built from the
+// kernels of dense_impl.cuh, and the four inversion algorithms.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "dense_impl.cuh"
+#include "ops.h"
+
+namespace frob {
+
+// ------------------------------------------------------------------ small kernels
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): state advanced by the
+// golden-ratio increment, then the published finaliser.  mu for matrix b and
+// draw `attempt` is the (b * 2^32 + attempt + 1)-th output for `seed`, mapped
+// to the open interval (0, 1) as ((z >> 11) + 0.5) * 2^-53.
+__host__ __device__ inline double draw_mu(uint64_t seed, int b, int attempt) {
+  uint64_t ctr = ((uint64_t)(uint32_t)b << 32) + (uint64_t)(uint32_t)attempt + 1ull;
+  uint64_t z = seed + ctr * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return ((double)(z >> 11) + 0.5) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ void init_info(frob_info* info, int b, double mu) {
+  if (info == nullptr) return;
+  frob_info f;
+  f.status = FROB_OK;
+  f.bad_index = 0;
+  f.ns_iters = 0;
+  f.fell_back = 0;
+  f.mu = mu;
+  f.residual = 0.0;
+  info[b] = f;
+}
+
+// M = A + iB (interleaved) -> planes A (two copies: one is factorised, one
+// becomes S) and B.  Almost sure variant (Sec. 4.2): A' = A - mu B,
+// B' = mu A + B.  HPD variant (Sec. 4.3): only the lower triangle is read;
+// A = Re (symmetric), B = Im (skew-symmetric, zero diagonal).
+template <typename R>
+__global__ void split_kernel(int n, MatB<const typename cplx_of<R>::type> M, MatB<R> A1, MatB<R> A2, MatB<R> Bp,
+                             frob_info* info, int hpd, int almost_sure, uint64_t seed, int attempt) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const double mu = almost_sure ? draw_mu(seed, b, attempt) : 0.0;
+  if (e == 0) init_info(info, b, mu);
+  const auto* Mb = M.at(b);
+  R a, bb;
+  if (hpd) {
+    if (i >= j) {
+      auto v = Mb[(int64_t)i * M.ld + j];
+      a = v.x;
+      bb = (i == j) ? (R)0 : v.y;
+    } else {
+      auto v = Mb[(int64_t)j * M.ld + i];
+      a = v.x;
+      bb = -v.y;
+    }
+  } else {
+    auto v = Mb[(int64_t)i * M.ld + j];
+    a = v.x;
+    bb = v.y;
+    if (almost_sure) {
+      R m = (R)mu;
+      R a2 = a - m * bb;
+      bb = m * a + bb;
+      a = a2;
+    }
+  }
+  A1.at(b)[(int64_t)i * A1.ld + j] = a;
+  if (A2.p) A2.at(b)[(int64_t)i * A2.ld + j] = a;
+  Bp.at(b)[(int64_t)i * Bp.ld + j] = bb;
+}
+
+// complex copy M -> W (baselines), with the info records initialised
+template <typename C>
+__global__ void copy_kernel(int n, MatB<const C> M, MatB<C> W, frob_info* info) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  if (e == 0) init_info(info, b, 0.0);
+  W.at(b)[(int64_t)i * W.ld + j] = M.at(b)[(int64_t)i * M.ld + j];
+}
+
+// rp = the permutation P of P A = L U as a row map: (P B)[r] = B[rp[r]].
+// Built by applying the recorded exchanges in order to the identity.
+static __global__ void rowperm_kernel(int n, const int* piv, int* rp, int use_smem) {
+  const int b = blockIdx.x;
+  extern __shared__ int sp[];
+  int* p = use_smem ? sp : rp + (int64_t)b * n;
+  const int* pv = piv + (int64_t)b * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n; ++k) {
+      int q = pv[k];
+      int x = p[k];
+      p[k] = p[q];
+      p[q] = x;
+    }
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rp[(int64_t)b * n + i] = p[i];
+}
+
+// X[:, rp[c]] = Z[:, c]   (M^{-1} = (U^{-1} L^{-1}) P)
+template <typename C>
+__global__ void colperm_kernel(int n, MatB<const C> Z, MatB<C> X, const int* rp) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), c = (int)(e % n);
+  X.at(b)[(int64_t)i * X.ld + rp[(int64_t)b * n + c]] = Z.at(b)[(int64_t)i * Z.ld + c];
+}
+
+// ------------------------------------------------------------------ launch helpers
+inline dim3 elem_grid(int n, int batch) {
+  int64_t nn = (int64_t)n * n;
+  return dim3((unsigned)((nn + 255) / 256), 1, (unsigned)batch);
+}
+
+constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+
+template <typename T> inline int panel_width() { return PANEL_MAX; }
+
+template <typename T, int OPA, int OPB, class Epi>
+inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<const T> B, Epi epi, int tile_mode,
+                        cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch);
+  FROB_LAUNCH("gemm_kernel", st, gemm_kernel<T, OPA, OPB, Epi><<<grid, NTH, 0, st>>>(M, N, K, A, B, epi, tile_mode));
+}
+
+template <typename T>
+inline EpiAxpby<T> axpby(MatB<T> D, T alpha, T beta, bool beta_zero) {
+  return EpiAxpby<T>{D, MatB<const T>{D.p, D.ld, D.bs}, alpha, beta, beta_zero ? 1 : 0};
+}
+
+template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
+inline void trsm_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SmemTrsm<T>));
+    done = true;
+  }
+}
+
+// op(T) X = B over all block rows (in order of the substitution)
+template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
+inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm, MatB<T> X, const int* rowperm,
+                 cudaStream_t st) {
+  trsm_smem_attr<T, OPT, LOWER, UNIT, RHS_I>();
+  const int nblk = (n + TB - 1) / TB;
+  dim3 grid((nrhs + TB - 1) / TB, 1, batch);
+  for (int s = 0; s < nblk; ++s) {
+    int kb = LOWER ? s : nblk - 1 - s;
+    FROB_LAUNCH("trsm_step_kernel", st, trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I><<<grid, NTH, sizeof(SmemTrsm<T>), st>>>(n, nrhs, kb, Tm, Bm, X,
+                                                                                       rowperm));
+  }
+}
+
+template <typename T> inline void panel_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(getrf_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX);
+    cudaFuncSetAttribute(potrf_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX);
+    cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)laswp_trsm_smem<T>());
+    done = true;
+  }
+}
+
+// Blocked right-looking LU with partial pivoting (P A = L U, in place).
+template <typename T>
+inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st) {
+  panel_smem_attr<T>();
+  const int nb = panel_width<T>();
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
+    const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
+    const int staged = bytes <= PANEL_SMEM_MAX;
+    FROB_LAUNCH("getrf_panel_kernel", st, getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info, info_off,
+                                                                            staged));
+    FROB_LAUNCH("laswp_trsm_kernel", st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
+    const int r = k0 + kb;
+    if (r < n) {
+      MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
+      MatB<const T> U12{A.p + (int64_t)k0 * A.ld + r, A.ld, A.bs};
+      MatB<T> A22 = A.sub(r, r);
+      gemm_launch<T, OP_N, OP_N>(n - r, n - r, kb, batch, L21, U12, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
+                                 0, st);
+    }
+  }
+}
+
+// Blocked right-looking Cholesky (A = L L^H, lower triangle, in place).
+template <typename T>
+inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cudaStream_t st) {
+  panel_smem_attr<T>();
+  const int nb = panel_width<T>();
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
+    const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
+    const int staged = bytes <= PANEL_SMEM_MAX;
+    FROB_LAUNCH("potrf_panel_kernel", st, potrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, info, info_off, staged));
+    const int r = k0 + kb;
+    if (r < n) {
+      MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
+      MatB<T> A22 = A.sub(r, r);
+      gemm_launch<T, OP_N, OP_C>(n - r, n - r, kb, batch, L21, L21, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
+                                 1, st);
+    }
+  }
+}
+
+inline void rowperm(int n, int batch, const int* piv, int* rp, cudaStream_t st) {
+  const int use_smem = (size_t)n * sizeof(int) <= 48 * 1024;
+  FROB_LAUNCH("rowperm_kernel", st, rowperm_kernel<<<batch, 256, use_smem ? n * sizeof(int) : 0, st>>>(n, piv, rp, use_smem));
+}
+
+// ------------------------------------------------------------------ workspace
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carve {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T> T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += align256(count * sizeof(T));
+    return p;
+  }
+};
+
+template <typename T> inline MatB<T> plane(Carve& c, int n, int batch) {
+  T* p = c.take<T>((size_t)n * n * batch);
+  return MatB<T>{p, n, (int64_t)n * n};
+}
+
+// ------------------------------------------------------------------ algorithms
+// Frobenius inversion with LU (Sec. 4.1).  R = double or float.
+template <typename R>
+size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  Planes<R> p;
+  p.LA = plane<R>(c, n, batch);
+  p.S = plane<R>(c, n, batch);
+  p.Bp = plane<R>(c, n, batch);
+  p.X1 = plane<R>(c, n, batch);
+  p.Y = plane<R>(c, n, batch);
+  p.piv1 = c.take<int>((size_t)n * batch);
+  p.piv2 = c.take<int>((size_t)n * batch);
+  p.rp1 = c.take<int>((size_t)n * batch);
+  p.rp2 = c.take<int>((size_t)n * batch);
+  if (out) *out = p;
+  return c.off;
+}
+
+template <typename R>
+void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
+                 const frob_opts& o, void* ws, frob_info* info, cudaStream_t st) {
+  Planes<R> p;
+  frob_lu_ws<R>(n, batch, ws, &p);
+  auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("split_kernel", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
+                                                       o.attempt));
+  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                       // A = P1^T L1 U1
+  rowperm(n, batch, p.piv1, p.rp1, st);
+  trsm<R, OP_N, true, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);   // L1 Y = P1 B
+  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st); // U1 X1 = Y
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.X1), axpby<R>(p.S, (R)1, (R)1, false), 0,
+                             st);                                                       // S = A + B X1
+  getrf<R>(n, batch, p.S, p.piv2, info, n, st);                                        // S = P2^T L2 U2
+  rowperm(n, batch, p.piv2, p.rp2, st);
+  trsm<R, OP_N, true, true, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // Y = L2^{-1}
+  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
+  EpiFrobOut<R> epi{X, cst(p.Y), p.rp2, n, o.almost_sure ? info : nullptr};
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.X1), cst(p.Y), epi, 0, st);          // X = Z P2 - i X1 Z P2
+}
+
+// Frobenius inversion with Cholesky (Sec. 4.3).
+template <typename R>
+size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  Planes<R> p{};
+  p.LA = plane<R>(c, n, batch);
+  p.S = plane<R>(c, n, batch);
+  p.Bp = plane<R>(c, n, batch);
+  p.Y = plane<R>(c, n, batch);
+  if (out) *out = p;
+  return c.off;
+}
+
+template <typename R>
+void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
+                   void* ws, frob_info* info, cudaStream_t st) {
+  Planes<R> p;
+  frob_chol_ws<R>(n, batch, ws, &p);
+  auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("split_kernel", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
+  potrf<R>(n, batch, p.LA, info, 0, st);                                                 // A = R1^T R1, L1 = R1^T
+  trsm<R, OP_N, true, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X1 = L1^{-1} B
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.Bp), axpby<R>(p.S, (R)-1, (R)1, false), 1,
+                             st);                                                         // S = A - X1^T X1
+  trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X2 = L1^{-T} X1
+  potrf<R>(n, batch, p.S, info, n, st);                                                  // S = R2^T R2
+  trsm<R, OP_N, true, false, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // X5 = L2^{-1}
+  trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);  // X6 = L2^{-T} X5
+  EpiFrobOut<R> epi{X, cst(p.Y), nullptr, n, nullptr};
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.Y), epi, 0, st);           // X = X6 - i X2 X6
+}
+
+// Complex LU inversion (Algorithm "Inversion with LU decomposition").
+template <typename C>
+size_t cplx_lu_ws(int n, int batch, void* ws, CPlanes<C>* out) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  CPlanes<C> p{};
+  p.W = plane<C>(c, n, batch);
+  p.Y = plane<C>(c, n, batch);
+  p.piv = c.take<int>((size_t)n * batch);
+  p.rp = c.take<int>((size_t)n * batch);
+  if (out) *out = p;
+  return c.off;
+}
+
+template <typename C>
+void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info, cudaStream_t st) {
+  CPlanes<C> p;
+  cplx_lu_ws<C>(n, batch, ws, &p);
+  auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("copy_kernel", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
+  getrf<C>(n, batch, p.W, p.piv, info, 0, st);                                           // M = P^T L U
+  rowperm(n, batch, p.piv, p.rp, st);
+  trsm<C, OP_N, true, true, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);     // Y = L^{-1}
+  trsm<C, OP_N, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);  // Z = U^{-1} Y
+  FROB_LAUNCH("colperm_kernel", st, colperm_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(p.Y), X, p.rp));          // X = Z P
+}
+
+// Complex Cholesky inversion (Algorithm "Inversion with Cholesky decomposition").
+template <typename C>
+size_t cplx_chol_ws(int n, int batch, void* ws, CPlanes<C>* out) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  CPlanes<C> p{};
+  p.W = plane<C>(c, n, batch);
+  p.Y = plane<C>(c, n, batch);
+  if (out) *out = p;
+  return c.off;
+}
+
+template <typename C>
+void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info, cudaStream_t st) {
+  CPlanes<C> p;
+  cplx_chol_ws<C>(n, batch, ws, &p);
+  auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("copy_kernel", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
+  potrf<C>(n, batch, p.W, info, 0, st);                                                  // M = R^H R, L = R^H
+  trsm<C, OP_N, true, false, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);    // X1 = L^{-1}
+  trsm<C, OP_C, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), X, nullptr, st);    // X2 = L^{-H} X1
+}
+
+}  // namespace frob

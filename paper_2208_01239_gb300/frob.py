@@ -1,0 +1,229 @@
+"""Thin ctypes binding over libfrobinv.so (the C ABI in include/frobinv.h).
+
+Argument marshalling only: every step of the inversion runs in the CUDA
+kernels of the library.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: if the library is missing or no CUDA
+device is present, the calls raise.
+
+The entry points keep the C names:
+
+* :func:`frob_inv`       Frobenius inversion (Sec. 4.1; almost sure variant
+                         of Sec. 4.2 with ``almost_sure=True``)
+* :func:`frob_inv_hpd`   Frobenius inversion of HPD matrices (Sec. 4.3)
+* :func:`cplx_lu_inv`    complex LU inversion baseline (Sec. 4)
+* :func:`cplx_chol_inv`  complex Cholesky inversion baseline (Sec. 4.3)
+
+Each takes a complex tensor of shape (n, n) or (batch, n, n), complex128 for
+``prec="fp64"`` and complex64 for ``prec="fp32"``, on the GPU or on the host
+(host tensors are copied to the device and the result back).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FROB_OK = 0
+FROB_ERR_ARG = 1
+FROB_ERR_SINGULAR = 2
+FROB_ERR_NOT_HPD = 3
+FROB_ERR_NOT_CONVERGED = 4
+FROB_ERR_TIMEOUT = 5
+FROB_ERR_CUDA = 6
+FROB_ERR_WORKSPACE = 7
+FROB_ERR_UNSUPPORTED = 8
+
+PREC = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+OP = {"frob_inv": 0, "frob_inv_hpd": 1, "cplx_lu_inv": 2, "cplx_chol_inv": 3}
+
+INFO_DTYPE = np.dtype([("status", "<i4"), ("bad_index", "<i4"), ("ns_iters", "<i4"), ("fell_back", "<i4"),
+                       ("mu", "<f8"), ("residual", "<f8")])
+assert INFO_DTYPE.itemsize == 32
+
+
+class FrobOpts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("almost_sure", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("attempt", ctypes.c_int32), ("ns_max_iter", ctypes.c_int32), ("ns_tol", ctypes.c_double)]
+
+
+class FrobError(RuntimeError):
+    """Raised for a non-OK status; ``status`` is the frob_status code and
+    ``info`` (if any) the per-matrix records."""
+
+    def __init__(self, msg, status, info=None):
+        super().__init__(msg)
+        self.status = status
+        self.info = info
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libfrobinv.so (built by ``paper_2208_01239_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfrobinv.so is not built ({path}); run python -m paper_2208_01239_gb300.build")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        lib.frob_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        lib.frob_workspace_bytes.restype = sz
+        common = [i32, i32, vp, i64, i64, vp, i64, i64]
+        for name in ("frob_inv", "frob_inv_hpd"):
+            f = getattr(lib, name)
+            f.argtypes = common + [ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
+            f.restype = i32
+        for name in ("cplx_lu_inv", "cplx_chol_inv"):
+            f = getattr(lib, name)
+            f.argtypes = common + [i32, vp, sz, vp, vp]
+            f.restype = i32
+        lib.frob_status_str.argtypes = [i32]
+        lib.frob_status_str.restype = ctypes.c_char_p
+        lib.frob_version.argtypes = []
+        lib.frob_version.restype = ctypes.c_char_p
+        lib.frob_kernel_launches.argtypes = []
+        lib.frob_kernel_launches.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def status_str(code: int) -> str:
+    return load().frob_status_str(int(code)).decode()
+
+
+def workspace_bytes(op: str, n: int, batch: int, prec: str = "fp64") -> int:
+    return int(load().frob_workspace_bytes(OP[op], n, batch, PREC[prec]))
+
+
+def _cdtype(prec: str):
+    return torch.complex64 if prec == "fp32" else torch.complex128
+
+
+def parse_info(info: torch.Tensor) -> np.ndarray:
+    """Device info records -> numpy structured array (synchronises)."""
+    return info.cpu().numpy().view(INFO_DTYPE).reshape(-1)
+
+
+def check_info(info_np: np.ndarray, what: str):
+    bad = np.nonzero(info_np["status"] != FROB_OK)[0]
+    if len(bad):
+        b = int(bad[0])
+        st = int(info_np["status"][b])
+        raise FrobError(f"{what}: matrix {b}: {status_str(st)} (bad_index={int(info_np['bad_index'][b])}); "
+                        f"{len(bad)} of {len(info_np)} matrices failed", st, info_np)
+
+
+class Result:
+    """Output of a call: the inverse and the device-side info records."""
+
+    def __init__(self, x: torch.Tensor, info: torch.Tensor):
+        self.x = x
+        self.info_dev = info
+
+    def info(self) -> np.ndarray:
+        return parse_info(self.info_dev)
+
+
+def _call(op: str, m: torch.Tensor, prec: str, opts: FrobOpts | None, out: torch.Tensor | None,
+          ws: torch.Tensor | None, info: torch.Tensor | None, check: bool) -> Result:
+    lib = load()
+    on_host = not m.is_cuda
+    if on_host:
+        m = m.pin_memory().to("cuda", non_blocking=True) if torch.cuda.is_available() else m.cuda()
+    if m.dtype != _cdtype(prec):
+        raise TypeError(f"{op}: expected {_cdtype(prec)} for prec={prec}, got {m.dtype}")
+    squeeze = m.dim() == 2
+    m3 = m.unsqueeze(0) if squeeze else m
+    if m3.dim() != 3 or m3.shape[-1] != m3.shape[-2]:
+        raise ValueError(f"{op}: expected (n, n) or (batch, n, n), got {tuple(m.shape)}")
+    if m3.stride(-1) != 1:
+        m3 = m3.contiguous()
+    batch, n = m3.shape[0], m3.shape[-1]
+    dev = m3.device
+    if out is None:
+        out3 = torch.empty((batch, n, n), dtype=m3.dtype, device=dev)
+    else:
+        out3 = out.unsqueeze(0) if out.dim() == 2 else out
+    need = int(lib.frob_workspace_bytes(OP[op], n, batch, PREC[prec]))
+    if ws is None:
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    base = ws.data_ptr()
+    pad = (-base) % 256
+    ws_ptr, ws_bytes = base + pad, ws.numel() - pad
+    if info is None:
+        info = torch.zeros((batch, 32), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    args = (n, batch, m3.data_ptr(), m3.stride(1), m3.stride(0), out3.data_ptr(), out3.stride(1), out3.stride(0))
+    with torch.cuda.device(dev):
+        if op in ("frob_inv", "frob_inv_hpd"):
+            st = getattr(lib, op)(*args, ctypes.byref(opts) if opts is not None else None, ws_ptr, ws_bytes,
+                                  info.data_ptr(), stream)
+        else:
+            st = getattr(lib, op)(*args, PREC[prec], ws_ptr, ws_bytes, info.data_ptr(), stream)
+    if st != FROB_OK:
+        raise FrobError(f"{op}: {status_str(st)}", st)
+    res = Result(out3[0] if (squeeze and out is None) else (out if out is not None else out3), info)
+    if check:
+        check_info(res.info(), op)
+    if on_host:
+        res.x = res.x.cpu()
+    return res
+
+
+def _opts(prec: str, almost_sure: bool = False, seed: int = 0, attempt: int = 0) -> FrobOpts:
+    o = FrobOpts()
+    o.prec = PREC[prec]
+    o.almost_sure = 1 if almost_sure else 0
+    o.seed = seed
+    o.attempt = attempt
+    o.ns_max_iter = 8
+    o.ns_tol = 1e-14
+    return o
+
+
+def frob_inv(m: torch.Tensor, prec: str = "fp64", almost_sure: bool = False, seed: int = 0, attempt: int = 0,
+             out=None, ws=None, info=None, check: bool = True) -> Result:
+    """(A + iB)^{-1} = S^{-1} - i A^{-1} B S^{-1}, S = A + B A^{-1} B."""
+    return _call("frob_inv", m, prec, _opts(prec, almost_sure, seed, attempt), out, ws, info, check)
+
+
+def frob_inv_hpd(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
+    """Frobenius inversion with two real Cholesky factorisations (HPD input,
+    lower triangle read)."""
+    return _call("frob_inv_hpd", m, prec, _opts(prec), out, ws, info, check)
+
+
+def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
+    """Complex LU inversion with partial pivoting (baseline)."""
+    return _call("cplx_lu_inv", m, prec, None, out, ws, info, check)
+
+
+def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
+    """Complex Cholesky inversion (HPD baseline, lower triangle read)."""
+    return _call("cplx_chol_inv", m, prec, None, out, ws, info, check)
+
+
+def draw_mu(seed: int, b: int, attempt: int = 0) -> float:
+    """Host copy of the library's SplitMix64 draw of mu (for reporting only;
+    the kernels draw mu themselves)."""
+    mask = (1 << 64) - 1
+    ctr = ((b & 0xFFFFFFFF) << 32) + (attempt & 0xFFFFFFFF) + 1
+    z = (seed + ctr * 0x9E3779B97F4A7C15) & mask
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    z ^= z >> 31
+    return ((z >> 11) + 0.5) * 2.0 ** -53
