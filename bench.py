@@ -33,7 +33,21 @@ BATCH = 64
 SEED = 2
 WORKLOAD = "hpd_batch64_n512_fp64"
 METRIC = "complex inversions/s (Frobenius-Cholesky vs complex Cholesky), 1 GB300, equal residual"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s
+
+
+def algorithmic_flops(n, batch):
+    """Real flops each kernel family of frob_inv_hpd must do per call (Sec. 4.3,
+    Algorithm "Frobenius inversion with Cholesky decomposition")."""
+    n3 = float(n) ** 3 * batch
+    return {
+        "trsm<f64,op1,upper>": 2 * n3,            # R1 X2 = X1 and R2 X6 = X5, n right-hand sides each
+        "gemm<f64,op0,op0,frob_out>": 2 * n3,     # X7 = X2 X6 (+ interleaved output)
+        "trsm<f64,op0,lower>": n3,                # R1^T X1 = B
+        "gemm<f64,op1,op0,axpby>": n3,            # S = A - X1^T X1 (one triangle)
+        "trsm<f64,op0,lower,rhs=I>": n3 / 3,      # R2^T X5 = I (X5 lower triangular)
+        "gemm<f64,op0,op2,axpby>": 2 * n3 / 3,    # trailing updates of the two Cholesky factorisations
+    }
 
 
 def _dist():
@@ -122,6 +136,13 @@ def run_reference(args):
     return 0
 
 
+def residual_fro(m, x):
+    """||M X - I||_F / (||M||_F ||X||_F) in FP64 (numpy)."""
+    import numpy as np
+    r = m @ x - np.eye(m.shape[0])
+    return float(np.linalg.norm(r) / (np.linalg.norm(m) * np.linalg.norm(x)))
+
+
 def cpu_baseline(ms, budget_s=12.0):
     """Oracle (plain C FP64 Frobenius-Cholesky) on a bounded sample."""
     import oracle
@@ -154,7 +175,6 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from oracle import metrics
     from paper_2208_01239_gb300 import build as fbuild
     from paper_2208_01239_gb300 import flops
     from paper_2208_01239_gb300 import frob
@@ -213,13 +233,17 @@ def main():
     inf = frob.parse_info(info)
     frob.check_info(inf, "frob_inv_hpd")
     x0 = x_dev.cpu().numpy()
-    res = max(metrics.residual_fro(ms[b], x0[b]) for b in (0, BATCH // 2, BATCH - 1))
+    res = max(residual_fro(ms[b], x0[b]) for b in (0, BATCH // 2, BATCH - 1))
 
-    # timed region (device): K steps, clocks sampled meanwhile
+    # timed region (device): K steps, clocks sampled meanwhile, per-kernel
+    # CUDA events recorded by the library on the launching stream
     launches0 = lib.frob_kernel_launches()
     clk = _clock_sampler()
     time.sleep(0.3)
+    frob.profile_enable(True)
     t_ms = timed(step, args.steps)
+    frob.profile_enable(False)
+    prof = frob.profile_report()
     clocks = _clock_summary(clk, local)
     launches = lib.frob_kernel_launches() - launches0
     ms_per_step = t_ms / args.steps
@@ -231,7 +255,7 @@ def main():
     tb_ms = timed(step_baseline, args.steps) / args.steps
     torch.cuda.synchronize(dev)
     xb = x_dev.cpu().numpy()
-    res_b = max(metrics.residual_fro(ms[b], xb[b]) for b in (0, BATCH // 2, BATCH - 1))
+    res_b = max(residual_fro(ms[b], xb[b]) for b in (0, BATCH // 2, BATCH - 1))
 
     # end to end through the public API with host buffers
     def e2e_step():
@@ -243,6 +267,18 @@ def main():
         e2e_step()
     te_ms = timed(e2e_step, args.steps) / args.steps
     bytes_io = BATCH * N_ORDER * N_ORDER * 16
+
+    # the dominant kernel family by device time, and its algorithmic rate
+    alg = algorithmic_flops(N_ORDER, BATCH)
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "kernel": top,
+            "peak_source": "FP64 DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; measured 1.19)"}
+    if top in alg:
+        launches_top, ms_top = prof[top]
+        ach = alg[top] * args.steps / (ms_top * 1e-3) / 1e12
+        roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS, launches_per_step=launches_top / args.steps,
+                    flops_per_step=alg[top], ms_per_launch=ms_top / launches_top)
 
     exec_flops = flops.executed("frob_chol", N_ORDER) * BATCH
     tflops_exec = exec_flops / (ms_per_step * 1e-3) / 1e12
@@ -259,10 +295,11 @@ def main():
         "baseline_gpu": {"name": "cplx_chol_inv", "value": world * BATCH / (tb_ms * 1e-3), "unit": "inversions/s",
                          "ms_per_step": tb_ms, "residual_fro_max_sampled": res_b,
                          "tflops_executed": flops.executed("cplx_chol", N_ORDER) * BATCH / (tb_ms * 1e-3) / 1e12},
-        "roofline": {"bound": "alu", "achieved": tflops_exec, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tflops_exec / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "whole step (every stage is FP64-pipe bound)",
-                     "peak_source": "FP64 DFMA: 152 SMs x 4 flop/clk x 2.07 GHz"},
+        "roofline": roof,
+        "path_roofline": {"bound": "alu", "achieved": tflops_exec, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": tflops_exec / FP64_PEAK_TFLOPS, "what": "whole step, executed FP64 flops"},
+        "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                        "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)} for k, v in prof.items()},
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),

@@ -162,6 +162,17 @@ const char* frob_version(void);
  * the kernels behind a call. */
 uint64_t frob_kernel_launches(void);
 
+/* Per-kernel device-time profiling (diagnostics, off by default).
+ * frob_profile_enable(1) discards earlier records and starts bracketing every
+ * kernel launch of the library with a pair of CUDA events recorded on the
+ * launching stream; frob_profile_enable(0) stops recording.
+ * frob_profile_report() waits for the recorded events, writes a JSON object
+ * {"<kernel variant>": [launches, total_ms], ...} into buf (truncated to len
+ * bytes, NUL-terminated), releases the records and returns the length needed
+ * including the NUL.  Not for use inside CUDA graph capture. */
+void frob_profile_enable(int on);
+size_t frob_profile_report(char* buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,10 @@
 // C-ABI entry points of libfrobinv (declared in include/frobinv.h): argument
 // checks, workspace sizing and dispatch to the per-precision drivers.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -22,14 +26,46 @@ static int debug_level() {
   }();
   return level;
 }
-void launch_begin(const char* name) {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::atomic<int> g_prof_on{0};
+static std::vector<ProfRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+static thread_local ProfRec t_pending{nullptr, nullptr, nullptr};
+
+static cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void launch_begin(const char* name, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (debug_level()) {
     std::fprintf(stderr, "[frob] launch %s\n", name);
     std::fflush(stderr);
   }
+  if (g_prof_on.load(std::memory_order_relaxed)) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    t_pending = ProfRec{name, prof_event(), prof_event()};
+    cudaEventRecord(t_pending.a, st);
+  }
 }
 void launch_end(const char* name, cudaStream_t st) {
+  if (t_pending.name == name && t_pending.a) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(t_pending.b, st);
+    g_prof_recs.push_back(t_pending);
+    t_pending = ProfRec{nullptr, nullptr, nullptr};
+  }
   if (debug_level()) {
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
@@ -185,5 +221,48 @@ const char* frob_status_str(int status) {
 const char* frob_version(void) { return "frobinv 0.1 sm_103a"; }
 
 uint64_t frob_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void frob_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (on) {
+    for (auto& r : g_prof_recs) {
+      g_prof_pool.push_back(r.a);
+      g_prof_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+  }
+  g_prof_on.store(on ? 1 : 0);
+}
+
+size_t frob_profile_report(char* buf, size_t len) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::map<std::string, std::pair<long, double>> acc;
+  for (auto& r : g_prof_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& e = acc[r.name];
+      e.first += 1;
+      e.second += ms;
+    }
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_recs.clear();
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : acc) {
+    char tmp[96];
+    std::snprintf(tmp, sizeof(tmp), "[%ld, %.6f]", kv.second.first, kv.second.second);
+    out += (first ? "\"" : ", \"") + kv.first + "\": " + tmp;
+    first = false;
+  }
+  out += "}";
+  if (buf && len) {
+    size_t k = out.size() < len - 1 ? out.size() : len - 1;
+    std::memcpy(buf, out.data(), k);
+    buf[k] = 0;
+  }
+  return out.size() + 1;
+}
 
 }  // extern "C"

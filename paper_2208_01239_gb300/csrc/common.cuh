@@ -144,14 +144,23 @@ enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
 // by launch_begin / launch_end, which count launches and, when the
 // environment variable FROB_DEBUG_SYNC is set to 1, log each launch to stderr,
 // synchronise the stream after it and log the CUDA status.
-void launch_begin(const char* name);
+// When profiling is on (frob_profile_enable), launch_begin / launch_end also
+// record a CUDA event pair on the launching stream, so that per-kernel device
+// time can be read back with frob_profile_report.
+void launch_begin(const char* name, cudaStream_t st);
 void launch_end(const char* name, cudaStream_t st);
-#define FROB_LAUNCH(NAME, ST, ...) \
-  do {                             \
-    ::frob::launch_begin(NAME);    \
-    __VA_ARGS__;                   \
-    ::frob::launch_end(NAME, ST);  \
+#define FROB_LAUNCH(NAME, ST, ...)    \
+  do {                                \
+    ::frob::launch_begin(NAME, ST);   \
+    __VA_ARGS__;                      \
+    ::frob::launch_end(NAME, ST);     \
   } while (0)
+
+template <typename T> constexpr const char* type_tag();
+template <> constexpr const char* type_tag<double>() { return "f64"; }
+template <> constexpr const char* type_tag<float>() { return "f32"; }
+template <> constexpr const char* type_tag<zd>() { return "c128"; }
+template <> constexpr const char* type_tag<zf>() { return "c64"; }
 
 // Per-matrix status written by the kernels (first failure wins).
 __device__ __forceinline__ void report(frob_info* info, int b, int status, int bad_index) {

@@ -123,6 +123,7 @@ __device__ __forceinline__ void mainloop(T (&acc)[4][4], SmemAB<T>& sm, const T*
 // Epilogue: D = alpha * acc + beta * C (C may alias D; C is not read when
 // beta_is_zero).
 template <typename T> struct EpiAxpby {
+  static constexpr const char* tag = "axpby";
   MatB<T> D;
   MatB<const T> C;
   T alpha, beta;
@@ -145,6 +146,7 @@ template <typename T> struct EpiAxpby {
 // dst = rowperm of P2 (S^{-1} = Z P2 moves column j of Z to column rp[j]);
 // NULL for no permutation (Cholesky variant).
 template <typename R> struct EpiFrobOut {
+  static constexpr const char* tag = "frob_out";
   using C = typename cplx_of<R>::type;
   MatB<C> X;
   MatB<const R> Z;

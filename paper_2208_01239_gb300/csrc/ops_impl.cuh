@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <string>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -137,7 +138,9 @@ inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<co
                         cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch);
-  FROB_LAUNCH("gemm_kernel", st, gemm_kernel<T, OPA, OPB, Epi><<<grid, NTH, 0, st>>>(M, N, K, A, B, epi, tile_mode));
+  static const std::string name = std::string("gemm<") + type_tag<T>() + ",op" + std::to_string(OPA) + ",op" +
+                                  std::to_string(OPB) + "," + Epi::tag + ">";
+  FROB_LAUNCH(name.c_str(), st, gemm_kernel<T, OPA, OPB, Epi><<<grid, NTH, 0, st>>>(M, N, K, A, B, epi, tile_mode));
 }
 
 template <typename T>
@@ -164,7 +167,10 @@ inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm,
   dim3 grid((nrhs + TB - 1) / TB, 1, batch);
   for (int s = 0; s < nblk; ++s) {
     int kb = LOWER ? s : nblk - 1 - s;
-    FROB_LAUNCH("trsm_step_kernel", st, trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I><<<grid, NTH, sizeof(SmemTrsm<T>), st>>>(n, nrhs, kb, Tm, Bm, X,
+    static const std::string name = std::string("trsm<") + type_tag<T>() + ",op" + std::to_string(OPT) +
+                                    (LOWER ? ",lower" : ",upper") + (UNIT ? ",unit" : "") + (RHS_I ? ",rhs=I" : "") +
+                                    ">";
+    FROB_LAUNCH(name.c_str(), st, trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I><<<grid, NTH, sizeof(SmemTrsm<T>), st>>>(n, nrhs, kb, Tm, Bm, X,
                                                                                        rowperm));
   }
 }
@@ -180,6 +186,19 @@ template <typename T> inline void panel_smem_attr() {
   }
 }
 
+template <typename T> inline const char* getrf_panel_name() {
+  static const std::string s = std::string("getrf_panel<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+template <typename T> inline const char* laswp_name() {
+  static const std::string s = std::string("laswp_trsm<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+template <typename T> inline const char* potrf_panel_name() {
+  static const std::string s = std::string("potrf_panel<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+
 // Blocked right-looking LU with partial pivoting (P A = L U, in place).
 template <typename T>
 inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st) {
@@ -189,9 +208,9 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
     const int kb = std::min(nb, n - k0);
     const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
-    FROB_LAUNCH("getrf_panel_kernel", st, getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info, info_off,
+    FROB_LAUNCH(getrf_panel_name<T>(), st, getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info, info_off,
                                                                             staged));
-    FROB_LAUNCH("laswp_trsm_kernel", st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
+    FROB_LAUNCH(laswp_name<T>(), st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
     const int r = k0 + kb;
     if (r < n) {
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
@@ -212,7 +231,7 @@ inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cu
     const int kb = std::min(nb, n - k0);
     const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
-    FROB_LAUNCH("potrf_panel_kernel", st, potrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, info, info_off, staged));
+    FROB_LAUNCH(potrf_panel_name<T>(), st, potrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, info, info_off, staged));
     const int r = k0 + kb;
     if (r < n) {
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
@@ -225,7 +244,7 @@ inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cu
 
 inline void rowperm(int n, int batch, const int* piv, int* rp, cudaStream_t st) {
   const int use_smem = (size_t)n * sizeof(int) <= 48 * 1024;
-  FROB_LAUNCH("rowperm_kernel", st, rowperm_kernel<<<batch, 256, use_smem ? n * sizeof(int) : 0, st>>>(n, piv, rp, use_smem));
+  FROB_LAUNCH("rowperm", st, rowperm_kernel<<<batch, 256, use_smem ? n * sizeof(int) : 0, st>>>(n, piv, rp, use_smem));
 }
 
 // ------------------------------------------------------------------ workspace
@@ -271,7 +290,7 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
   Planes<R> p;
   frob_lu_ws<R>(n, batch, ws, &p);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
-  FROB_LAUNCH("split_kernel", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
+  FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
                                                        o.attempt));
   getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                       // A = P1^T L1 U1
   rowperm(n, batch, p.piv1, p.rp1, st);
@@ -306,7 +325,7 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
   Planes<R> p;
   frob_chol_ws<R>(n, batch, ws, &p);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
-  FROB_LAUNCH("split_kernel", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
+  FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
   potrf<R>(n, batch, p.LA, info, 0, st);                                                 // A = R1^T R1, L1 = R1^T
   trsm<R, OP_N, true, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X1 = L1^{-1} B
   gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.Bp), axpby<R>(p.S, (R)-1, (R)1, false), 1,
@@ -337,12 +356,12 @@ void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_in
   CPlanes<C> p;
   cplx_lu_ws<C>(n, batch, ws, &p);
   auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
-  FROB_LAUNCH("copy_kernel", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
+  FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
   getrf<C>(n, batch, p.W, p.piv, info, 0, st);                                           // M = P^T L U
   rowperm(n, batch, p.piv, p.rp, st);
   trsm<C, OP_N, true, true, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);     // Y = L^{-1}
   trsm<C, OP_N, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);  // Z = U^{-1} Y
-  FROB_LAUNCH("colperm_kernel", st, colperm_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(p.Y), X, p.rp));          // X = Z P
+  FROB_LAUNCH("colperm", st, colperm_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(p.Y), X, p.rp));          // X = Z P
 }
 
 // Complex Cholesky inversion (Algorithm "Inversion with Cholesky decomposition").
@@ -361,7 +380,7 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   CPlanes<C> p;
   cplx_chol_ws<C>(n, batch, ws, &p);
   auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
-  FROB_LAUNCH("copy_kernel", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
+  FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
   potrf<C>(n, batch, p.W, info, 0, st);                                                  // M = R^H R, L = R^H
   trsm<C, OP_N, true, false, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);    // X1 = L^{-1}
   trsm<C, OP_C, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), X, nullptr, st);    // X2 = L^{-H} X1

@@ -97,8 +97,28 @@ def load() -> ctypes.CDLL:
         lib.frob_version.restype = ctypes.c_char_p
         lib.frob_kernel_launches.argtypes = []
         lib.frob_kernel_launches.restype = ctypes.c_uint64
+        lib.frob_profile_enable.argtypes = [i32]
+        lib.frob_profile_enable.restype = None
+        lib.frob_profile_report.argtypes = [ctypes.c_char_p, sz]
+        lib.frob_profile_report.restype = sz
         _lib = lib
         return lib
+
+
+def profile_enable(on: bool = True):
+    """Start (discarding earlier records) or stop per-kernel event timing."""
+    load().frob_profile_enable(1 if on else 0)
+
+
+def profile_report() -> dict:
+    """{kernel variant: (launches, total device ms)} since profile_enable."""
+    import json
+    lib = load()
+    buf = ctypes.create_string_buffer(1 << 20)
+    need = int(lib.frob_profile_report(buf, len(buf)))
+    if need > len(buf):
+        raise RuntimeError("profile report truncated")
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
 def status_str(code: int) -> str:
