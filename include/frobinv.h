@@ -151,6 +151,35 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
 frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
                           int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream);
 
+/*
+ * frob_inv_hpd_noalloc -- frob_inv_hpd in FP64 for callers that cannot
+ * allocate device memory (no counterpart in the paper: this is a deployment
+ * variant).  Some callers own no allocator: a plugin inside a framework that
+ * manages every device buffer itself, a latency-bound loop in which a
+ * cudaMalloc could stall the device, or a foreign-language caller without a
+ * device allocator.  They pass only the input M, the output X and the info
+ * records; the workspace is a 32 MiB scratch array inside the library,
+ * allocated on every GPU that loads the library and held until the process
+ * exits.
+ *
+ * Arguments and results are those of frob_inv_hpd with prec = FROB_FP64.
+ * The problem must fit the scratch: frob_workspace_bytes(FROB_OP_INV_HPD, n,
+ * batch, FROB_FP64) <= 32 MiB, i.e. about n * n * batch <= 2^20 (n = 1024 with
+ * batch 1, n = 512 with batch 4); larger problems return FROB_ERR_WORKSPACE
+ * and launch nothing.  Other argument errors return FROB_ERR_ARG.
+ *
+ * The first call made with a given device current looks up the scratch
+ * array's device address on that device; make that first call before any
+ * stream capture.  The function itself calls no cudaMalloc, cudaFree or other
+ * allocating routine.  All calls share the one scratch array, which keeps
+ * whatever the last call left in it (no call depends on its contents):
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads without ordering -- race on it and give wrong
+ * results.
+ */
+frob_status frob_inv_hpd_noalloc(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
+                                 int64_t sx, frob_info* info, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 
