@@ -180,6 +180,21 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
 frob_status frob_inv_hpd_noalloc(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
                                  int64_t sx, frob_info* info, void* stream);
 
+/*
+ * frob_gemm_tc -- the tensor-core GEMM building block (no counterpart in the
+ * paper; it serves the mixed-precision forms): C[b] = A[b] . B[b]^T with
+ * A (M x K) and B (N x K) row-major FP32 on the device, both rounded to
+ * nearest into BF16 (kind 0) or TF32 (kind 1) in the workspace, multiplied
+ * by tcgen05.mma with FP32 accumulation in tensor memory, C (M x N) FP32.
+ * `err` is a device int set to FROB_ERR_TIMEOUT if a bounded wait inside the
+ * kernel gave up (0 otherwise; the caller zeroes it).  Workspace:
+ * frob_gemm_tc_workspace_bytes(kind, M, N, K, batch) bytes, 256-aligned.
+ */
+frob_status frob_gemm_tc(int kind, int M, int N, int K, int batch, const float* A, int64_t lda, int64_t sa,
+                         const float* B, int64_t ldb, int64_t sb, float* C, int64_t ldc, int64_t sc, void* ws,
+                         size_t wsb, int* err, void* stream);
+size_t frob_gemm_tc_workspace_bytes(int kind, int M, int N, int K, int batch);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 

@@ -1,0 +1,141 @@
+// Host side of the tensor-core GEMM: operand conversion (FP32 -> BF16 or
+// TF32, round to nearest, K-major with a 16-byte aligned row pitch), TMA
+// tensor maps, launch, and the C-ABI entry point frob_gemm_tc.
+#include <cstdint>
+#include <cstring>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+
+#include "../../include/frobinv.h"
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace frob {
+namespace tc {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// rank-3 map over [batch][rows][K] with row pitch `pitch` elements
+bool make_map(CUtensorMap* map, const void* ptr, int kind, int K, int rows, int batch, int64_t pitch,
+              int64_t bpitch, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int elem = kind == 0 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)(pitch * elem), (cuuint64_t)(bpitch * elem)};
+  cuuint32_t box[3] = {(cuuint32_t)(BK_BYTES / elem), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_TFLOAT32, 3,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// src (rows x K, row-major, ld) -> dst (rows x pitch), BF16 or TF32-rounded FP32
+template <int KIND>
+__global__ void convert_kernel(int rows, int K, const float* src, int64_t ld, int64_t sb, void* dst, int64_t pitch) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * pitch) return;
+  const int r = (int)(e / pitch), k = (int)(e % pitch);
+  const float v = k < K ? src[(int64_t)b * sb + (int64_t)r * ld + k] : 0.f;
+  const int64_t o = (int64_t)b * rows * pitch + e;
+  if (KIND == 0)
+    static_cast<__nv_bfloat16*>(dst)[o] = __float2bfloat16_rn(v);
+  else
+    static_cast<float*>(dst)[o] = to_tf32(v);
+}
+
+template <int KIND, int BN, int STAGES, class Epi>
+cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, int batch, Epi epi, int* err,
+                   cudaStream_t st) {
+  using S = TcSmem<BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         S::BYTES);
+    attr = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  FROB_LAUNCH(KIND == 0 ? "tc_gemm<bf16>" : "tc_gemm<tf32>", st,
+              tc_gemm_kernel<KIND, BN, STAGES, Epi><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K, epi, err));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t pitch_for(int kind, int K) {
+  const int q = kind == 0 ? 8 : 4;  // 16 bytes
+  return ((int64_t)K + q - 1) / q * q;
+}
+
+size_t gemm_tc_ws(int kind, int M, int N, int K, int batch) {
+  const int64_t p = pitch_for(kind, K);
+  const size_t elem = kind == 0 ? 2 : 4;
+  auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return a256((size_t)batch * M * p * elem) + a256((size_t)batch * N * p * elem) + 256;
+}
+
+}  // namespace tc
+}  // namespace frob
+
+using namespace frob;
+
+extern "C" frob_status frob_gemm_tc(int kind, int M, int N, int K, int batch, const float* A, int64_t lda, int64_t sa,
+                                    const float* B, int64_t ldb, int64_t sb, float* C, int64_t ldc, int64_t sc,
+                                    void* ws, size_t wsb, int* err, void* stream) {
+  if ((kind != 0 && kind != 1) || M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535) return FROB_ERR_ARG;
+  if (!A || !B || !C || !err || lda < K || ldb < K || ldc < N) return FROB_ERR_ARG;
+  const size_t need = tc::gemm_tc_ws(kind, M, N, K, batch);
+  if (!ws || wsb < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return FROB_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t p = tc::pitch_for(kind, K);
+  const size_t elem = kind == 0 ? 2 : 4;
+  unsigned char* wa = static_cast<unsigned char*>(ws);
+  unsigned char* wb = wa + (((size_t)batch * M * p * elem + 255) & ~(size_t)255);
+  {
+    dim3 ga((unsigned)(((int64_t)M * p + 255) / 256), 1, batch), gb((unsigned)(((int64_t)N * p + 255) / 256), 1, batch);
+    if (kind == 0) {
+      FROB_LAUNCH("tc_convert<bf16>", st, tc::convert_kernel<0><<<ga, 256, 0, st>>>(M, K, A, lda, sa, wa, p));
+      FROB_LAUNCH("tc_convert<bf16>", st, tc::convert_kernel<0><<<gb, 256, 0, st>>>(N, K, B, ldb, sb, wb, p));
+    } else {
+      FROB_LAUNCH("tc_convert<tf32>", st, tc::convert_kernel<1><<<ga, 256, 0, st>>>(M, K, A, lda, sa, wa, p));
+      FROB_LAUNCH("tc_convert<tf32>", st, tc::convert_kernel<1><<<gb, 256, 0, st>>>(N, K, B, ldb, sb, wb, p));
+    }
+  }
+  CUtensorMap ma, mb;
+  if (!tc::make_map(&ma, wa, kind, K, M, batch, p, (int64_t)M * p, tc::BM) ||
+      !tc::make_map(&mb, wb, kind, K, N, batch, p, (int64_t)N * p, 128))
+    return FROB_ERR_CUDA;
+  tc::TcEpiStoreF32 epi{C, ldc, sc, 1.f, 0.f};
+  cudaError_t e = kind == 0 ? tc::launch<0, 128, 4>(ma, mb, M, N, K, batch, epi, err, st)
+                            : tc::launch<1, 128, 4>(ma, mb, M, N, K, batch, epi, err, st);
+  return e == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;
+}
+
+extern "C" size_t frob_gemm_tc_workspace_bytes(int kind, int M, int N, int K, int batch) {
+  if ((kind != 0 && kind != 1) || M < 1 || N < 1 || K < 1 || batch < 1) return 0;
+  return frob::tc::gemm_tc_ws(kind, M, N, K, batch);
+}

@@ -97,6 +97,11 @@ def load() -> ctypes.CDLL:
         lib.frob_version.restype = ctypes.c_char_p
         lib.frob_kernel_launches.argtypes = []
         lib.frob_kernel_launches.restype = ctypes.c_uint64
+        lib.frob_gemm_tc.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, sz, vp,
+                                     vp]
+        lib.frob_gemm_tc.restype = i32
+        lib.frob_gemm_tc_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
+        lib.frob_gemm_tc_workspace_bytes.restype = sz
         lib.frob_profile_enable.argtypes = [i32]
         lib.frob_profile_enable.restype = None
         lib.frob_profile_report.argtypes = [ctypes.c_char_p, sz]
@@ -235,6 +240,40 @@ def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=Non
 def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
     """Complex Cholesky inversion (HPD baseline, lower triangle read)."""
     return _call("cplx_chol_inv", m, prec, None, out, ws, info, check)
+
+
+def gemm_tc(a: torch.Tensor, b: torch.Tensor, kind: str = "bf16", out: torch.Tensor | None = None,
+            ws: torch.Tensor | None = None) -> torch.Tensor:
+    """C = A B^T on the tensor cores (tcgen05): A (batch, M, K), B (batch, N, K)
+    FP32 on the GPU, rounded to BF16 or TF32 (round to nearest), FP32
+    accumulation.  Returns C (batch, M, N) FP32."""
+    lib = load()
+    k = {"bf16": 0, "tf32": 1}[kind]
+    a3 = a if a.dim() == 3 else a.unsqueeze(0)
+    b3 = b if b.dim() == 3 else b.unsqueeze(0)
+    if a3.dtype != torch.float32 or b3.dtype != torch.float32 or not a3.is_cuda:
+        raise TypeError("gemm_tc: FP32 CUDA tensors expected")
+    batch, M, K = a3.shape
+    N = b3.shape[1]
+    if a3.stride(-1) != 1:
+        a3 = a3.contiguous()
+    if b3.stride(-1) != 1:
+        b3 = b3.contiguous()
+    c3 = torch.empty((batch, M, N), dtype=torch.float32, device=a3.device) if out is None else out
+    need = int(lib.frob_gemm_tc_workspace_bytes(k, M, N, K, batch))
+    if ws is None:
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=a3.device)
+    pad = (-ws.data_ptr()) % 256
+    err = torch.zeros(1, dtype=torch.int32, device=a3.device)
+    st = lib.frob_gemm_tc(k, M, N, K, batch, a3.data_ptr(), a3.stride(1), a3.stride(0), b3.data_ptr(), b3.stride(1),
+                          b3.stride(0), c3.data_ptr(), c3.stride(1), c3.stride(0), ws.data_ptr() + pad,
+                          ws.numel() - pad, err.data_ptr(), torch.cuda.current_stream(a3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"gemm_tc: {status_str(st)}", st)
+    e = int(err.item())
+    if e != 0:
+        raise FrobError(f"gemm_tc: device status {status_str(e)}", e)
+    return c3 if (a.dim() == 3 or out is not None) else c3[0]
 
 
 def draw_mu(seed: int, b: int, attempt: int = 0) -> float:
