@@ -24,6 +24,10 @@ of Dai, Lim and Ye, "Complex matrix inversion via real matrix inversions":
 * :func:`frob_inv_chol` -- Algorithm "Frobenius inversion with Cholesky
                            decomposition" (Sec. 4.3).
 * :func:`inv2x2`, :func:`adjugate_inv` -- closed forms used as pins.
+* :func:`inv_adjoint`   -- -X^H G X^H, the gradient of a real loss through
+                           X = M^{-1} (from d(M^{-1}) = -M^{-1} dM M^{-1}).
+* :func:`sign_newton`   -- Newton's iteration for the matrix sign function
+                           (Sec. 5.3, eq. "iter"), fixed step count.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against values fixed by
 mathematics (closed forms, brute force, identities from the paper, LAPACK via
@@ -114,6 +118,8 @@ class Oracle:
             "orc_inv2x2": [zp, zp],
             "orc_adjugate_inv": [i, zp, zp],
             "orc_num_threads": [],
+            "orc_inv_adjoint": [i, zp, zp, zp],
+            "orc_sign_newton": [i, zp, i, zp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -189,6 +195,24 @@ class Oracle:
         """OpenMP threads the oracle uses (1 if built without OpenMP)."""
         return int(self.lib.orc_num_threads())
 
+    def inv_adjoint(self, x, g) -> np.ndarray:
+        """-X^H G X^H: the gradient with respect to M of a real loss whose
+        gradient with respect to X = M^{-1} is G."""
+        x, n = _prep(x)
+        g, n2 = _prep(g)
+        if n != n2:
+            raise ValueError("shape mismatch")
+        out = np.empty_like(x)
+        _check("inv_adjoint", self.lib.orc_inv_adjoint(n, _ptr(x), _ptr(g), _ptr(out)))
+        return out
+
+    def sign_newton(self, m, iters: int) -> np.ndarray:
+        """`iters` Newton steps X <- (X + X^{-1})/2 from X = M (Sec. 5.3)."""
+        m, n = _prep(m)
+        out = np.empty_like(m)
+        _check("sign_newton", self.lib.orc_sign_newton(n, _ptr(m), int(iters), _ptr(out)))
+        return out
+
 
 def load(mutant: int = 0) -> Oracle:
     """The oracle bound to the normal build (mutant=0) or a planted-mistake
@@ -232,6 +256,14 @@ def adjugate_inv(m):
 
 def num_threads() -> int:
     return load().num_threads()
+
+
+def inv_adjoint(x, g):
+    return load().inv_adjoint(x, g)
+
+
+def sign_newton(m, iters: int):
+    return load().sign_newton(m, iters)
 
 
 from . import metrics  # noqa: E402,F401

@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORC_MUTANT plants one deliberate mistake (k = 1..7) so that a test can check
+/* ORC_MUTANT plants one deliberate mistake (k = 1..9) so that a test can check
  * that the pins catch it.  Product builds of the oracle use ORC_MUTANT = 0. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -563,6 +563,55 @@ int orc_adjugate_inv(int n, const zc *m, zc *x)
             zc cof = (((i + j) & 1) ? -1.0 : 1.0) * zdet_laplace(n - 1, minor);
             x[(size_t)i * n + j] = cof / det;
         }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of inversion: for X = M^{-1} and a real loss with gradient G with  */
+/* respect to X (G = dL/dRe X + i dL/dIm X), the gradient with respect to M   */
+/* is -X^H G X^H, from d(M^{-1}) = -M^{-1} dM M^{-1}.  Plain triple loops.    */
+/* ------------------------------------------------------------------------- */
+int orc_inv_adjoint(int n, const zc *x, const zc *g, zc *out)
+{
+    if (n < 1) return -2;
+    zc *p = malloc(sizeof(zc) * (size_t)n * n);
+    if (!p) return -1;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)          /* P = X^H G */
+        for (int j = 0; j < n; ++j) {
+            zc s = 0.0;
+            for (int k = 0; k < n; ++k) s += (ORC_MUTANT == 8 ? x[IDX(k, i)] : conj(x[IDX(k, i)])) * g[IDX(k, j)];
+            p[IDX(i, j)] = s;
+        }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)          /* out = -P X^H */
+        for (int j = 0; j < n; ++j) {
+            zc s = 0.0;
+            for (int k = 0; k < n; ++k) s += p[IDX(i, k)] * conj(x[IDX(j, k)]);
+            out[IDX(i, j)] = -s;
+        }
+    free(p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Newton iteration for the matrix sign function (Sec. 5.3, eq. "iter"):      */
+/* X_{k+1} = (X_k + X_k^{-1}) / 2, X_0 = M, a fixed number of steps, each     */
+/* inverse by complex LU (right inverse).                                     */
+/* ------------------------------------------------------------------------- */
+int orc_sign_newton(int n, const zc *m, int iters, zc *out)
+{
+    if (n < 1 || iters < 0) return -2;
+    size_t nn = (size_t)n * n;
+    zc *xi = malloc(sizeof(zc) * nn);
+    if (!xi) return -1;
+    memcpy(out, m, sizeof(zc) * nn);
+    for (int k = 0; k < iters; ++k) {
+        int info = orc_cplx_lu_inv(n, out, xi, 0);
+        if (info) { free(xi); return info; }
+        for (size_t t = 0; t < nn; ++t) out[t] = (ORC_MUTANT == 9 ? 1.0 : 0.5) * (out[t] + xi[t]);
+    }
+    free(xi);
     return 0;
 }
 

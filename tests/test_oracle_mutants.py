@@ -22,6 +22,8 @@ MUTANTS = {
     5: "X1 X1^T instead of X1^T X1 (Frobenius with Cholesky)",
     6: "X3 + mu X4 instead of X3 - mu X4 (almost sure un-rotation)",
     7: "column swaps in forward order (left LU inverse)",
+    8: "X^T instead of X^H in the adjoint",
+    9: "X + X^{-1} instead of (X + X^{-1})/2 in the sign iteration",
 }
 
 
@@ -60,6 +62,25 @@ def _pin_failures(o) -> list:
                 fails.append(f"hpd {name}")
         except oracle.OracleError:
             fails.append(f"hpd {name} raised")
+    # adjoint against central finite differences of the inverse
+    n = 6
+    m = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)) + 4 * np.eye(n)
+    gg = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    d = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    h = 1e-5
+    ip = lambda a, b: float(np.sum((np.conj(a) * b).real))
+    fd = (ip(gg, o.cplx_lu_inv(m + h * d)) - ip(gg, o.cplx_lu_inv(m - h * d))) / (2 * h)
+    an = ip(o.inv_adjoint(o.cplx_lu_inv(m), gg), d)
+    if abs(fd - an) > 1e-7 * max(1.0, abs(an)):
+        fails.append("adjoint finite differences")
+    # sign iteration against sign(Z J Z^{-1}) = Z sign(Re J) Z^{-1}
+    re = np.array([1.0, 1.5, -0.7, -2.0])
+    j = re + 1j * np.array([0.3, -0.2, 0.5, 0.1])
+    z = g.standard_normal((4, 4)) + 3 * np.eye(4)
+    x = z @ np.diag(j) @ np.linalg.inv(z)
+    sref = z @ np.diag(np.sign(re)) @ np.linalg.inv(z)
+    if np.abs(o.sign_newton(x, 40) - sref).max() > 1e-9 * np.abs(sref).max():
+        fails.append("sign closed form")
     return fails
 
 
