@@ -70,7 +70,8 @@ typedef enum {
   FROB_OP_INV = 0,       /* frob_inv */
   FROB_OP_INV_HPD = 1,   /* frob_inv_hpd */
   FROB_OP_CPLX_LU = 2,   /* cplx_lu_inv */
-  FROB_OP_CPLX_CHOL = 3  /* cplx_chol_inv */
+  FROB_OP_CPLX_CHOL = 3, /* cplx_chol_inv */
+  FROB_OP_ADJOINT = 4    /* frob_inv_adjoint */
 } frob_op;
 
 typedef struct {
@@ -194,6 +195,20 @@ frob_status frob_gemm_tc(int kind, int M, int N, int K, int batch, const float* 
                          const float* B, int64_t ldb, int64_t sb, float* C, int64_t ldc, int64_t sc, void* ws,
                          size_t wsb, int* err, void* stream);
 size_t frob_gemm_tc_workspace_bytes(int kind, int M, int N, int K, int batch);
+
+/*
+ * frob_inv_adjoint -- reverse-mode derivative of inversion: for X = M^{-1}
+ * and the gradient G of a real loss with respect to X (G = dL/dRe X +
+ * i dL/dIm X, PyTorch's convention), writes gradM = -X^H G X^H, which follows
+ * from d(M^{-1}) = -M^{-1} dM M^{-1}.  Computed as two complex products, each
+ * with Gauss's three real multiplications (Sec. 2, Proposition "matrix
+ * mult"), on the CUDA cores.  X, G, gradM: strided batches like frob_inv's,
+ * complex128 (prec FROB_FP64) or complex64 (FROB_FP32); gradM must not
+ * overlap X or G.  Workspace: frob_workspace_bytes(FROB_OP_ADJOINT, ...).
+ */
+frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64_t sx, const void* G, int64_t ldg,
+                             int64_t sg, void* gradM, int64_t ldr, int64_t sr, int prec, void* ws, size_t wsb,
+                             void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);

@@ -103,9 +103,10 @@ bool overlaps(const void* a, int64_t lda, int64_t sa, const void* b, int64_t ldb
 }
 
 frob_status check_common(int n, int batch, const void* M, int64_t ldm, int64_t sm, const void* X, int64_t ldx,
-                         int64_t sx, void* ws, size_t wsb, size_t need, frob_info* info, int prec) {
+                         int64_t sx, void* ws, size_t wsb, size_t need, frob_info* info, int prec,
+                         bool need_info = true) {
   if (n < 1 || batch < 1 || batch > 65535) return FROB_ERR_ARG;
-  if (!M || !X || !info) return FROB_ERR_ARG;
+  if (!M || !X || (need_info && !info)) return FROB_ERR_ARG;
   if (ldm < n || ldx < n) return FROB_ERR_ARG;
   if (batch > 1 && (sm < ldm * (int64_t)n || sx < ldx * (int64_t)n)) return FROB_ERR_ARG;
   if (overlaps(M, ldm, sm, X, ldx, sx, n, batch, elem_bytes(prec))) return FROB_ERR_ARG;
@@ -142,6 +143,8 @@ size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
       return f32 ? cplx_lu_ws<zf>(n, batch, nullptr, nullptr) : cplx_lu_ws<zd>(n, batch, nullptr, nullptr);
     case FROB_OP_CPLX_CHOL:
       return f32 ? cplx_chol_ws<zf>(n, batch, nullptr, nullptr) : cplx_chol_ws<zd>(n, batch, nullptr, nullptr);
+    case FROB_OP_ADJOINT:
+      return f32 ? adjoint_ws<float>(n, batch) : adjoint_ws<double>(n, batch);
     default:
       return 0;
   }
@@ -200,6 +203,23 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
     cplx_chol_run<zf>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
   else
     cplx_chol_run<zd>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  return launched();
+}
+
+frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64_t sx, const void* G, int64_t ldg,
+                             int64_t sg, void* gradM, int64_t ldr, int64_t sr, int prec, void* ws, size_t wsb,
+                             void* stream) {
+  if (!G || ldg < n || (batch > 1 && sg < ldg * (int64_t)n)) return FROB_ERR_ARG;
+  frob_status s = check_common(n, batch, X, ldx, sx, gradM, ldr, sr, ws, wsb,
+                               frob_workspace_bytes(FROB_OP_ADJOINT, n, batch, prec), nullptr, prec, false);
+  if (s != FROB_OK) return s;
+  if (overlaps(G, ldg, sg, gradM, ldr, sr, n, batch, elem_bytes(prec))) return FROB_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == FROB_FP32)
+    adjoint_run<float>(n, batch, in_view<zf>(X, ldx, sx), in_view<zf>(G, ldg, sg), out_view<zf>(gradM, ldr, sr), ws, st);
+  else
+    adjoint_run<double>(n, batch, in_view<zd>(X, ldx, sx), in_view<zd>(G, ldg, sg), out_view<zd>(gradM, ldr, sr), ws,
+                        st);
   return launched();
 }
 

@@ -39,4 +39,9 @@ template <typename C> size_t cplx_chol_ws(int n, int batch, void* ws, CPlanes<C>
 template <typename C> void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info,
                                          cudaStream_t st);
 
+template <typename R> size_t adjoint_ws(int n, int batch);
+template <typename R>
+void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB<const typename cplx_of<R>::type> G,
+                 MatB<typename cplx_of<R>::type> out, void* ws, cudaStream_t st);
+
 }  // namespace frob

@@ -386,4 +386,88 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   trsm<C, OP_C, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), X, nullptr, st);    // X2 = L^{-H} X1
 }
 
+// ------------------------------------------------------------------ adjoint
+// grad M = -X^H G X^H for X = M^{-1} (d(M^{-1}) = -M^{-1} dM M^{-1}), as two
+// complex products, each by Gauss's three real multiplications (Sec. 2,
+// Proposition "matrix mult"):
+//   P = X^H G:  T1 = Xr^T Gr, T2 = Xi^T Gi, T3 = (Xr - Xi)^T (Gr + Gi)
+//               Re P = T1 + T2, Im P = T3 - T1 + T2
+//   Q = P X^H:  U1 = Pr Xr^T, U2 = Pi Xi^T, U3 = (Pr + Pi)(Xr - Xi)^T
+//               Re Q = U1 + U2, Im Q = U3 - U1 + U2
+//   grad = -Q
+template <typename R>
+__global__ void adj_split_kernel(int n, MatB<const typename cplx_of<R>::type> X,
+                                 MatB<const typename cplx_of<R>::type> G, MatB<R> Xr, MatB<R> Xi, MatB<R> Xd,
+                                 MatB<R> Gr, MatB<R> Gi, MatB<R> Gs) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  auto x = X.at(b)[(int64_t)i * X.ld + j];
+  auto g = G.at(b)[(int64_t)i * G.ld + j];
+  const int64_t o = (int64_t)i * Xr.ld + j;
+  Xr.at(b)[o] = x.x;
+  Xi.at(b)[o] = x.y;
+  Xd.at(b)[o] = x.x - x.y;
+  Gr.at(b)[o] = g.x;
+  Gi.at(b)[o] = g.y;
+  Gs.at(b)[o] = g.x + g.y;
+}
+
+// in place: (T1, T2, T3) -> (Re P, Im P, Re P + Im P)
+template <typename R>
+__global__ void adj_combine_kernel(int n, MatB<R> T1, MatB<R> T2, MatB<R> T3) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int64_t o = (e / n) * T1.ld + (e % n);
+  const R t1 = T1.at(b)[o], t2 = T2.at(b)[o], t3 = T3.at(b)[o];
+  const R pr = t1 + t2, pi = t3 - t1 + t2;
+  T1.at(b)[o] = pr;
+  T2.at(b)[o] = pi;
+  T3.at(b)[o] = pr + pi;
+}
+
+template <typename R>
+__global__ void adj_out_kernel(int n, MatB<const R> U1, MatB<const R> U2, MatB<const R> U3,
+                               MatB<typename cplx_of<R>::type> out) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const int64_t o = (int64_t)i * U1.ld + j;
+  const R u1 = U1.at(b)[o], u2 = U2.at(b)[o], u3 = U3.at(b)[o];
+  typename cplx_of<R>::type v;
+  v.x = -(u1 + u2);
+  v.y = -(u3 - u1 + u2);
+  out.at(b)[(int64_t)i * out.ld + j] = v;
+}
+
+template <typename R> size_t adjoint_ws(int n, int batch) {
+  Carve c{nullptr};
+  for (int k = 0; k < 9; ++k) plane<R>(c, n, batch);
+  return c.off;
+}
+
+template <typename R>
+void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB<const typename cplx_of<R>::type> G,
+                 MatB<typename cplx_of<R>::type> out, void* ws, cudaStream_t st) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  MatB<R> P[9];
+  for (int k = 0; k < 9; ++k) P[k] = plane<R>(c, n, batch);
+  MatB<R>&Xr = P[0], &Xi = P[1], &Xd = P[2], &Gr = P[3], &Gi = P[4], &Gs = P[5], &T1 = P[6], &T2 = P[7], &T3 = P[8];
+  auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  const R one = (R)1, zero = (R)0;
+  FROB_LAUNCH("adj_split", st, adj_split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, X, G, Xr, Xi, Xd, Gr, Gi, Gs));
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(Xr), cst(Gr), axpby<R>(T1, one, zero, true), 0, st);
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(Xi), cst(Gi), axpby<R>(T2, one, zero, true), 0, st);
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(Xd), cst(Gs), axpby<R>(T3, one, zero, true), 0, st);
+  FROB_LAUNCH("adj_combine", st, adj_combine_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, T1, T2, T3));
+  // U1 -> Gr, U2 -> Gi, U3 -> Gs (the G planes are free now)
+  gemm_launch<R, OP_N, OP_T>(n, n, n, batch, cst(T1), cst(Xr), axpby<R>(Gr, one, zero, true), 0, st);
+  gemm_launch<R, OP_N, OP_T>(n, n, n, batch, cst(T2), cst(Xi), axpby<R>(Gi, one, zero, true), 0, st);
+  gemm_launch<R, OP_N, OP_T>(n, n, n, batch, cst(T3), cst(Xd), axpby<R>(Gs, one, zero, true), 0, st);
+  FROB_LAUNCH("adj_out", st, adj_out_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(Gr), cst(Gi), cst(Gs), out));
+}
+
 }  // namespace frob

@@ -39,7 +39,7 @@ FROB_ERR_WORKSPACE = 7
 FROB_ERR_UNSUPPORTED = 8
 
 PREC = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
-OP = {"frob_inv": 0, "frob_inv_hpd": 1, "cplx_lu_inv": 2, "cplx_chol_inv": 3}
+OP = {"frob_inv": 0, "frob_inv_hpd": 1, "cplx_lu_inv": 2, "cplx_chol_inv": 3, "frob_inv_adjoint": 4}
 
 INFO_DTYPE = np.dtype([("status", "<i4"), ("bad_index", "<i4"), ("ns_iters", "<i4"), ("fell_back", "<i4"),
                        ("mu", "<f8"), ("residual", "<f8")])
@@ -97,6 +97,8 @@ def load() -> ctypes.CDLL:
         lib.frob_version.restype = ctypes.c_char_p
         lib.frob_kernel_launches.argtypes = []
         lib.frob_kernel_launches.restype = ctypes.c_uint64
+        lib.frob_inv_adjoint.argtypes = common + [vp, i64, i64, i32, vp, sz, vp]
+        lib.frob_inv_adjoint.restype = i32
         lib.frob_gemm_tc.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, sz, vp,
                                      vp]
         lib.frob_gemm_tc.restype = i32
@@ -240,6 +242,33 @@ def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=Non
 def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
     """Complex Cholesky inversion (HPD baseline, lower triangle read)."""
     return _call("cplx_chol_inv", m, prec, None, out, ws, info, check)
+
+
+def inv_adjoint(x: torch.Tensor, g: torch.Tensor, prec: str | None = None) -> torch.Tensor:
+    """grad_M = -X^H G X^H for X = M^{-1} and the gradient G of a real loss
+    with respect to X (the library's frob_inv_adjoint kernel)."""
+    lib = load()
+    if prec is None:
+        prec = "fp32" if x.dtype == torch.complex64 else "fp64"
+    if x.dtype != _cdtype(prec) or g.dtype != x.dtype or not x.is_cuda:
+        raise TypeError("inv_adjoint: X and G must be CUDA tensors of the same complex dtype")
+    x3 = (x if x.dim() == 3 else x.unsqueeze(0))
+    g3 = (g if g.dim() == 3 else g.unsqueeze(0))
+    if x3.stride(-1) != 1:
+        x3 = x3.contiguous()
+    if g3.stride(-1) != 1:
+        g3 = g3.contiguous()
+    batch, n = x3.shape[0], x3.shape[-1]
+    out = torch.empty((batch, n, n), dtype=x3.dtype, device=x3.device)
+    need = int(lib.frob_workspace_bytes(OP["frob_inv_adjoint"], n, batch, PREC[prec]))
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=x3.device)
+    pad = (-ws.data_ptr()) % 256
+    st = lib.frob_inv_adjoint(n, batch, x3.data_ptr(), x3.stride(1), x3.stride(0), g3.data_ptr(), g3.stride(1),
+                              g3.stride(0), out.data_ptr(), out.stride(1), out.stride(0), PREC[prec],
+                              ws.data_ptr() + pad, ws.numel() - pad, torch.cuda.current_stream(x3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"inv_adjoint: {status_str(st)}", st)
+    return out if x.dim() == 3 else out[0]
 
 
 def gemm_tc(a: torch.Tensor, b: torch.Tensor, kind: str = "bf16", out: torch.Tensor | None = None,
