@@ -87,6 +87,7 @@ frob_opts default_opts() {
 }
 
 bool valid_prec(int p) { return p == FROB_FP64 || p == FROB_FP32; }
+bool mixed_prec(int p) { return p == FROB_MIXED_TF32 || p == FROB_MIXED_BF16; }
 
 size_t elem_bytes(int prec) { return prec == FROB_FP32 ? 8 : 16; }
 
@@ -110,7 +111,7 @@ frob_status check_common(int n, int batch, const void* M, int64_t ldm, int64_t s
   if (ldm < n || ldx < n) return FROB_ERR_ARG;
   if (batch > 1 && (sm < ldm * (int64_t)n || sx < ldx * (int64_t)n)) return FROB_ERR_ARG;
   if (overlaps(M, ldm, sm, X, ldx, sx, n, batch, elem_bytes(prec))) return FROB_ERR_ARG;
-  if (!valid_prec(prec)) return FROB_ERR_UNSUPPORTED;
+  if (!valid_prec(prec) && !mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
   if (!ws || wsb < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return FROB_ERR_WORKSPACE;
   return FROB_OK;
 }
@@ -132,7 +133,9 @@ template <typename T> MatB<T> out_view(void* p, int64_t ld, int64_t s) {
 extern "C" {
 
 size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
-  if (n < 1 || batch < 1 || !valid_prec(prec)) return 0;
+  if (n < 1 || batch < 1) return 0;
+  if (mixed_prec(prec)) return (op == FROB_OP_INV && n <= 512) ? mixed::mixed_ws(n, batch) : 0;
+  if (!valid_prec(prec)) return 0;
   const bool f32 = prec == FROB_FP32;
   switch (op) {
     case FROB_OP_INV:
@@ -158,6 +161,11 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
                                frob_workspace_bytes(FROB_OP_INV, n, batch, o.prec), info, o.prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mixed_prec(o.prec)) {
+    if (o.almost_sure) return FROB_ERR_UNSUPPORTED;
+    frob_status ms = mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st);
+    return ms != FROB_OK ? ms : launched();
+  }
   if (o.prec == FROB_FP32)
     frob_lu_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), o, ws, info, st);
   else
@@ -169,6 +177,7 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
                          const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
   frob_opts o = opts ? *opts : default_opts();
   if (o.almost_sure) return FROB_ERR_ARG;  // A is SPD for HPD input (Lemma "positive real part")
+  if (mixed_prec(o.prec)) return FROB_ERR_UNSUPPORTED;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_INV_HPD, n, batch, o.prec), info, o.prec);
   if (s != FROB_OK) return s;
@@ -182,6 +191,7 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
 
 frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
                         int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
+  if (mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_CPLX_LU, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
@@ -195,6 +205,7 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
 
 frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
                           int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
+  if (mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_CPLX_CHOL, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
@@ -209,6 +220,7 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
 frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64_t sx, const void* G, int64_t ldg,
                              int64_t sg, void* gradM, int64_t ldr, int64_t sr, int prec, void* ws, size_t wsb,
                              void* stream) {
+  if (mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
   if (!G || ldg < n || (batch > 1 && sg < ldg * (int64_t)n)) return FROB_ERR_ARG;
   frob_status s = check_common(n, batch, X, ldx, sx, gradM, ldr, sr, ws, wsb,
                                frob_workspace_bytes(FROB_OP_ADJOINT, n, batch, prec), nullptr, prec, false);

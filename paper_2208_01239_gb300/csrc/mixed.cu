@@ -1,0 +1,288 @@
+// Mixed-precision Frobenius inversion with Newton-Schulz refinement.
+//
+//   X_0      = Frobenius inversion of M in FP32 (Sec. 4.1, on the CUDA cores)
+//   repeat:  R = I - M X        FP64-accurate (digit-split products on the
+//                               BF16 tensor cores, ozaki.cuh)
+//            stop when ||R||_F / (||M||_F ||X||_F) <= tol
+//            X <- X + X R       (4 digits per operand: ~2^-28 relative, ample
+//                               for a correction that is itself ~||R|| X)
+//
+// X is kept in FP64 (planes X and X^T, so that both products only ever split
+// rows).  Matrices that have converged, or whose FP32 inversion failed, are
+// skipped by every later kernel through a per-matrix flag, so the loop needs
+// no host synchronisation and a fixed launch sequence.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/frobinv.h"
+#include "common.cuh"
+#include "ops.h"
+#include "ozaki.cuh"
+
+namespace frob {
+namespace mixed {
+
+constexpr int S_RESID = 7;
+constexpr int S_CORR = 4;
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    tried = true;
+  }
+  return fn;
+}
+
+// digits [2][S][batch][n][Kp] BF16 as a rank-3 map (Kp, n, 2 S batch)
+bool digit_map(CUtensorMap* map, const __nv_bfloat16* ptr, int n, int Kp, int S, int batch, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)n, (cuuint64_t)(2 * S * batch)};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)n * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)oz::KB, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// M (c128) -> M32 (c64) and FP64 planes [2][batch][n][n]; ||M||_F^2 per matrix
+__global__ void conv_in_kernel(int n, MatB<const zd> M, MatB<zf> M32, double* Mp, double* nM2) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  double ss = 0.0;
+  if (e < nn) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const zd v = M.at(b)[(int64_t)i * M.ld + j];
+    M32.at(b)[(int64_t)i * M32.ld + j] = zf{(float)v.x, (float)v.y};
+    Mp[(int64_t)b * nn + e] = v.x;
+    Mp[((int64_t)gridDim.z + b) * nn + e] = v.y;
+    ss = v.x * v.x + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0 && ss != 0.0) atomicAdd(nM2 + b, ss);
+}
+
+// X32 (c64) -> planes X, X^T (FP64)
+__global__ void conv_x_kernel(int n, MatB<const zf> X32, double* Xp, double* XTp, int batch) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  if (e >= nn) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const zf v = X32.at(b)[(int64_t)i * X32.ld + j];
+  Xp[(int64_t)b * nn + e] = v.x;
+  Xp[((int64_t)batch + b) * nn + e] = v.y;
+  XTp[(int64_t)b * nn + (int64_t)j * n + i] = v.x;
+  XTp[((int64_t)batch + b) * nn + (int64_t)j * n + i] = v.y;
+}
+
+// planes X -> interleaved c128 output
+__global__ void conv_out_kernel(int n, const double* Xp, MatB<zd> X, int batch) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  if (e >= nn) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  X.at(b)[(int64_t)i * X.ld + j] = zd{Xp[(int64_t)b * nn + e], Xp[((int64_t)batch + b) * nn + e]};
+}
+
+// ||X||_F^2 per matrix into nX2, and zero the residual accumulators
+__global__ void xnorm_kernel(int n, const double* Xp, double* nX2, double* rn2, int batch, const int* skip) {
+  const int b = blockIdx.z;
+  if (skip[b]) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  // FP32 is ample for the norm in a relative residual, and keeps the work
+  // off the FP64 pipe
+  float ss = 0.f;
+  if (e < nn) {
+    const float a = (float)Xp[(int64_t)b * nn + e], c = (float)Xp[((int64_t)batch + b) * nn + e];
+    ss = a * a + c * c;
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0 && ss != 0.f) atomicAdd(nX2 + b, (double)ss);
+}
+
+__global__ void zero_kernel(double* a, double* c, int batch, const int* skip) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch && !skip[b]) {
+    a[b] = 0.0;
+    c[b] = 0.0;
+  }
+}
+
+// skip matrices whose FP32 inversion failed
+__global__ void init_skip_kernel(const frob_info* info, int* skip, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) skip[b] = info[b].status != FROB_OK;
+}
+
+// relative residual, convergence and iteration bookkeeping
+__global__ void check_kernel(int batch, int it, int last, double tol, const double* rn2, const double* nM2,
+                             const double* nX2, int* skip, frob_info* info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch || skip[b]) return;
+  const double res = sqrt(rn2[b]) / (sqrt(nM2[b]) * sqrt(nX2[b]));
+  info[b].residual = res;
+  info[b].ns_iters = it;
+  if (res <= tol) {
+    skip[b] = 1;
+  } else if (last || !(res < 0.5)) {
+    // not converged within the budget, or the start was too poor for the
+    // iteration to contract (rho(I - M X_0) must be below 1)
+    info[b].status = FROB_ERR_NOT_CONVERGED;
+    skip[b] = 1;
+  }
+}
+
+template <int MODE>
+void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs& a, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(oz::oz_cgemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+    attr = true;
+  }
+  dim3 grid((a.n + oz::BN - 1) / oz::BN, (a.n + tc::BM - 1) / tc::BM, 2 * a.batch);
+  FROB_LAUNCH(MODE == oz::RESID ? "oz_cgemm<resid>" : "oz_cgemm<corr>", st,
+              oz::oz_cgemm_kernel<MODE><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ma, mb, a));
+}
+
+void launch_split(int n, int Kp, int batch, int S, const double* src, __nv_bfloat16* dst, int* exps,
+                  const int* skip, cudaStream_t st) {
+  const int64_t warps = (int64_t)2 * batch * n;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
+  FROB_LAUNCH("oz_split", st,
+              oz::oz_split_rows_kernel<<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
+                                                                   (int64_t)batch * n * n, dst, exps, skip));
+}
+
+struct Layout {
+  zf *M32, *X32;
+  void* ws32;
+  double *Mp, *Xp, *XTp, *RTp;
+  __nv_bfloat16 *Mdig, *Xdig, *Bdig;
+  int *expM, *expX, *expB;
+  double *rn2, *nM2, *nX2;
+  int *skip, *err;
+  size_t bytes;
+};
+
+Layout carve(int n, int batch, void* ws) {
+  Layout L{};
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  const size_t nn = (size_t)n * n;
+  const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
+  L.M32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
+  L.X32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
+  L.ws32 = take(frob_lu_ws<float>(n, batch, nullptr, nullptr));
+  L.Mp = static_cast<double*>(take(2 * nn * batch * 8));
+  L.Xp = static_cast<double*>(take(2 * nn * batch * 8));
+  L.XTp = static_cast<double*>(take(2 * nn * batch * 8));
+  L.RTp = static_cast<double*>(take(2 * nn * batch * 8));
+  const size_t dig = (size_t)2 * oz::S_MAX * batch * n * Kp * 2;
+  L.Mdig = static_cast<__nv_bfloat16*>(take(dig));
+  L.Xdig = static_cast<__nv_bfloat16*>(take(dig));
+  L.Bdig = static_cast<__nv_bfloat16*>(take(dig));
+  L.expM = static_cast<int*>(take((size_t)2 * batch * n * 4));
+  L.expX = static_cast<int*>(take((size_t)2 * batch * n * 4));
+  L.expB = static_cast<int*>(take((size_t)2 * batch * n * 4));
+  L.rn2 = static_cast<double*>(take((size_t)batch * 8));
+  L.nM2 = static_cast<double*>(take((size_t)batch * 8));
+  L.nX2 = static_cast<double*>(take((size_t)batch * 8));
+  L.skip = static_cast<int*>(take((size_t)batch * 4));
+  L.err = static_cast<int*>(take(256));
+  L.bytes = off;
+  return L;
+}
+
+}  // namespace
+
+size_t mixed_ws(int n, int batch) { return carve(n, batch, nullptr).bytes; }
+
+frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
+                      cudaStream_t st) {
+  if (n > oz::K_MAX) return FROB_ERR_UNSUPPORTED;
+  Layout L = carve(n, batch, ws);
+  const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
+  const int64_t nn = (int64_t)n * n;
+  const dim3 eg((unsigned)((nn + 255) / 256), 1, batch);
+  const double tol = o.ns_tol > 0 ? o.ns_tol : 1e-14;
+  const int max_iter = o.ns_max_iter > 0 ? o.ns_max_iter : 8;
+
+  cudaMemsetAsync(L.nM2, 0, (size_t)batch * 8, st);
+  cudaMemsetAsync(L.err, 0, 4, st);
+  FROB_LAUNCH("mixed_conv_in", st,
+              conv_in_kernel<<<eg, 256, 0, st>>>(n, M, MatB<zf>{L.M32, n, nn}, L.Mp, L.nM2));
+  // X_0: Frobenius inversion in FP32 (also initialises info)
+  frob_opts o32 = o;
+  o32.prec = FROB_FP32;
+  frob_lu_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, o32, L.ws32, info, st);
+  FROB_LAUNCH("mixed_conv_x", st, conv_x_kernel<<<eg, 256, 0, st>>>(n, MatB<const zf>{L.X32, n, nn}, L.Xp, L.XTp, batch));
+  FROB_LAUNCH("mixed_init_skip", st, init_skip_kernel<<<(batch + 127) / 128, 128, 0, st>>>(info, L.skip, batch));
+  launch_split(n, Kp, batch, S_RESID, L.Mp, L.Mdig, L.expM, L.skip, st);
+
+  CUtensorMap mapM, mapXT7, mapX3, mapRT3;
+  if (!digit_map(&mapM, L.Mdig, n, Kp, S_RESID, batch, tc::BM) ||
+      !digit_map(&mapXT7, L.Bdig, n, Kp, S_RESID, batch, oz::BN) ||
+      !digit_map(&mapX3, L.Xdig, n, Kp, S_CORR, batch, tc::BM) ||
+      !digit_map(&mapRT3, L.Bdig, n, Kp, S_CORR, batch, oz::BN))
+    return FROB_ERR_CUDA;
+
+  oz::OzArgs ra{};
+  ra.n = n;
+  ra.Kp = Kp;
+  ra.batch = batch;
+  ra.S = S_RESID;
+  ra.expA = L.expM;
+  ra.expB = L.expB;
+  ra.outR = L.RTp;
+  ra.rnorm2 = L.rn2;
+  ra.skip = L.skip;
+  ra.err = L.err;
+  oz::OzArgs ca = ra;
+  ca.S = S_CORR;
+  ca.expA = L.expX;
+  ca.X = L.Xp;
+  ca.XT = L.XTp;
+
+  for (int it = 0; it <= max_iter; ++it) {
+    FROB_LAUNCH("mixed_zero", st, zero_kernel<<<(batch + 127) / 128, 128, 0, st>>>(L.rn2, L.nX2, batch, L.skip));
+    FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<eg, 256, 0, st>>>(n, L.Xp, L.nX2, L.rn2, batch, L.skip));
+    launch_split(n, Kp, batch, S_RESID, L.XTp, L.Bdig, L.expB, L.skip, st);
+    launch_cgemm<oz::RESID>(mapM, mapXT7, ra, st);                                   // R = I - M X
+    FROB_LAUNCH("mixed_check", st,
+                check_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, it, it == max_iter, tol, L.rn2, L.nM2, L.nX2,
+                                                                  L.skip, info));
+    if (it == max_iter) break;
+    launch_split(n, Kp, batch, S_CORR, L.Xp, L.Xdig, L.expX, L.skip, st);
+    launch_split(n, Kp, batch, S_CORR, L.RTp, L.Bdig, L.expB, L.skip, st);
+    launch_cgemm<oz::CORR>(mapX3, mapRT3, ca, st);                                   // X <- X + X R
+  }
+  FROB_LAUNCH("mixed_conv_out", st, conv_out_kernel<<<eg, 256, 0, st>>>(n, L.Xp, X, batch));
+  return cudaGetLastError() == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;
+}
+
+}  // namespace mixed
+}  // namespace frob

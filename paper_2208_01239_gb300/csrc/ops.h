@@ -44,4 +44,11 @@ template <typename R>
 void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB<const typename cplx_of<R>::type> G,
                  MatB<typename cplx_of<R>::type> out, void* ws, cudaStream_t st);
 
+namespace mixed {
+// Mixed-precision Frobenius inversion with Newton-Schulz refinement (n <= 512).
+size_t mixed_ws(int n, int batch);
+frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
+                      cudaStream_t st);
+}  // namespace mixed
+
 }  // namespace frob

@@ -1,0 +1,88 @@
+"""Mixed-precision Frobenius inversion (FP32 start, Newton-Schulz refinement
+with FP64-accurate residuals on the BF16 tensor cores) against the oracle.
+
+The result must meet the FP64 targets: ||M X - I||_F/(||M||_F ||X||_F) <=
+1e-13, and a forward error against the oracle's complex LU inverse within
+32 n kappa(M) u64 plus kappa times the residual at which the refinement stops
+(its tolerance is 1e-14).  The residual the refinement measured on the device
+(info.residual, from the digit-split products) must agree with the residual
+recomputed in FP64 on the host, to the resolution of both.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import metrics
+from paper_2208_01239_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2208_01239_gb300 import build, frob
+    build.build()
+    frob.load()
+    return frob
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_tf32"])
+@pytest.mark.parametrize("n", [1, 7, 33, 64, 100, 128, 200, 256, 512])
+def test_mixed_vs_oracle(F, prec, n):
+    batch = 3 if n <= 256 else 2
+    ms = W.gaussian(n, batch=batch, seed=7000 + n)
+    r = F.frob_inv(torch.from_numpy(ms).cuda(), prec=prec)
+    x = r.x.cpu().numpy()
+    info = r.info()
+    for b in range(batch):
+        ref = oracle.cplx_lu_inv(ms[b])
+        res = metrics.residual_fro(ms[b], x[b])
+        assert res <= 1e-13, res
+        # refinement stops at the tolerance (1e-14), so the forward error is
+        # bounded by kappa times the attained residual (plus FP64 rounding)
+        kappa = np.linalg.cond(ms[b])
+        assert metrics.forward_error(x[b], ref) <= 32 * n * kappa * U64 + 4 * np.sqrt(n) * kappa * res
+        # the device-side residual (49-bit digit products, resolution ~2^-48
+        # relative to |M||X|) agrees with the host's FP64 evaluation (itself
+        # noisy at ~sqrt(n) u at this level)
+        tol = 0.05 * res + 2.0 ** -48 + 4 * np.sqrt(n) * U64
+        assert abs(info["residual"][b] - res) <= tol, (info["residual"][b], res)
+        assert info["ns_iters"][b] >= 1 or n == 1
+
+
+def test_mixed_hpd_workload_kappa_1e4(F):
+    """The HPD workload (kappa up to 1e4) through the general mixed route."""
+    ms, qs, lams = W.hpd(256, batch=4, seed=21, return_parts=True)
+    r = F.frob_inv(torch.from_numpy(ms).cuda(), prec="mixed_bf16")
+    x = r.x.cpu().numpy()
+    for b in range(4):
+        exact = W.hpd_exact_inverse(qs[b], lams[b])
+        kappa = lams[b].max() / lams[b].min()
+        assert metrics.residual_fro(ms[b], x[b]) <= 1e-13
+        assert metrics.forward_error(x[b], exact) <= 32 * 256 * kappa * U64
+
+
+def test_mixed_reports_failure_instead_of_wrong_result(F):
+    """kappa(M) ~ 2e6 with S = (1 - s^2) I: the FP32 start cannot resolve S.
+    Every matrix is either refined to the FP64 target or reported
+    FROB_ERR_NOT_CONVERGED; none is returned as OK with a poor residual."""
+    m, _ = W.ill_conditioned(64, seed=3)
+    ms = np.stack([m, W.gaussian(64, 1, seed=5)[0]])
+    r = F.frob_inv(torch.from_numpy(ms).cuda(), prec="mixed_bf16", check=False)
+    x = r.x.cpu().numpy()
+    info = r.info()
+    for b in range(2):
+        if info["status"][b] == F.FROB_OK:
+            assert metrics.residual_fro(ms[b], x[b]) <= 1e-13
+        else:
+            assert info["status"][b] == F.FROB_ERR_NOT_CONVERGED
+    assert info["status"][1] == F.FROB_OK
+
+
+def test_mixed_rejects_large_n(F):
+    m = torch.zeros((1, 520, 520), dtype=torch.complex128, device="cuda")
+    with pytest.raises(F.FrobError) as e:
+        F.frob_inv(m, prec="mixed_bf16", ws=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+    assert e.value.status in (F.FROB_ERR_UNSUPPORTED, F.FROB_ERR_WORKSPACE, F.FROB_ERR_ARG)
