@@ -115,7 +115,15 @@ size_t frob_workspace_bytes(int op, int n, int batch, int prec);
  *   n, batch   order and number of matrices (n >= 1, batch >= 1)
  *   M, ldm, sm input base, leading dimension (>= n), batch stride (elements)
  *   X, ldx, sx output base, leading dimension, batch stride (elements)
- *   opts       NULL or options (precision FROB_FP64 or FROB_FP32)
+ *   opts       NULL or options.  FROB_FP64 / FROB_FP32: the algorithm in that
+ *              precision.  FROB_MIXED_BF16 / FROB_MIXED_TF32 (n <= 512,
+ *              complex128 in and out): X0 by the FP32 algorithm, then
+ *              Newton-Schulz refinement X <- X + X (I - M X) until
+ *              ||I - M X||_F/(||M||_F ||X||_F) <= opts->ns_tol, at most
+ *              opts->ns_max_iter corrections; the products are FP64-accurate
+ *              (exact digit products on the BF16 tensor cores).  A matrix that
+ *              does not reach the tolerance gets FROB_ERR_NOT_CONVERGED;
+ *              info.ns_iters and info.residual report the iteration.
  *   ws, wsb    device workspace and its size in bytes
  *   info       device array of `batch` frob_info records (written)
  */
@@ -130,7 +138,8 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
  * A = R1^T R1; R1^T X1 = B; R1 X2 = X1; S = A - X1^T X1 (= A + B A^{-1} B);
  * S = R2^T R2; R2^T X5 = I; R2 X6 = X5; X = X6 - i X2 X6, both triangles
  * written.  Fails per matrix with FROB_ERR_NOT_HPD (bad_index = k for A,
- * n + k for S).  Arguments as for frob_inv.
+ * n + k for S).  Arguments as for frob_inv.  The mixed precisions (n <= 512)
+ * start from this algorithm in FP32 and refine like frob_inv's mixed modes.
  */
 frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
                          const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream);

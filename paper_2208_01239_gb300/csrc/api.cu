@@ -134,7 +134,8 @@ extern "C" {
 
 size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
   if (n < 1 || batch < 1) return 0;
-  if (mixed_prec(prec)) return (op == FROB_OP_INV && n <= 512) ? mixed::mixed_ws(n, batch) : 0;
+  if (mixed_prec(prec))
+    return ((op == FROB_OP_INV || op == FROB_OP_INV_HPD) && n <= 512) ? mixed::mixed_ws(n, batch) : 0;
   if (!valid_prec(prec)) return 0;
   const bool f32 = prec == FROB_FP32;
   switch (op) {
@@ -163,7 +164,8 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mixed_prec(o.prec)) {
     if (o.almost_sure) return FROB_ERR_UNSUPPORTED;
-    frob_status ms = mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st);
+    frob_status ms =
+        mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, false);
     return ms != FROB_OK ? ms : launched();
   }
   if (o.prec == FROB_FP32)
@@ -177,11 +179,16 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
                          const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
   frob_opts o = opts ? *opts : default_opts();
   if (o.almost_sure) return FROB_ERR_ARG;  // A is SPD for HPD input (Lemma "positive real part")
-  if (mixed_prec(o.prec)) return FROB_ERR_UNSUPPORTED;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_INV_HPD, n, batch, o.prec), info, o.prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mixed_prec(o.prec)) {
+    if (n > 512) return FROB_ERR_UNSUPPORTED;
+    frob_status ms =
+        mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, true);
+    return ms != FROB_OK ? ms : launched();
+  }
   if (o.prec == FROB_FP32)
     frob_chol_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
   else

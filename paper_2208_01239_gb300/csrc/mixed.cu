@@ -60,14 +60,22 @@ bool digit_map(CUtensorMap* map, const __nv_bfloat16* ptr, int n, int Kp, int S,
 }
 
 // M (c128) -> M32 (c64) and FP64 planes [2][batch][n][n]; ||M||_F^2 per matrix
-__global__ void conv_in_kernel(int n, MatB<const zd> M, MatB<zf> M32, double* Mp, double* nM2) {
+__global__ void conv_in_kernel(int n, MatB<const zd> M, MatB<zf> M32, double* Mp, double* nM2, int hpd) {
   const int b = blockIdx.z;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nn = (int64_t)n * n;
   double ss = 0.0;
   if (e < nn) {
     const int i = (int)(e / n), j = (int)(e % n);
-    const zd v = M.at(b)[(int64_t)i * M.ld + j];
+    zd v;
+    if (!hpd || i > j) {
+      v = M.at(b)[(int64_t)i * M.ld + j];
+    } else if (i == j) {
+      v = zd{M.at(b)[(int64_t)i * M.ld + j].x, 0.0};  // Hermitian: real diagonal
+    } else {
+      const zd w = M.at(b)[(int64_t)j * M.ld + i];   // upper triangle from the lower one
+      v = zd{w.x, -w.y};
+    }
     M32.at(b)[(int64_t)i * M32.ld + j] = zf{(float)v.x, (float)v.y};
     Mp[(int64_t)b * nn + e] = v.x;
     Mp[((int64_t)gridDim.z + b) * nn + e] = v.y;
@@ -196,7 +204,9 @@ Layout carve(int n, int batch, void* ws) {
   const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
   L.M32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
   L.X32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
-  L.ws32 = take(frob_lu_ws<float>(n, batch, nullptr, nullptr));
+  const size_t w_lu = frob_lu_ws<float>(n, batch, nullptr, nullptr);
+  const size_t w_ch = frob_chol_ws<float>(n, batch, nullptr, nullptr);
+  L.ws32 = take(w_lu > w_ch ? w_lu : w_ch);
   L.Mp = static_cast<double*>(take(2 * nn * batch * 8));
   L.Xp = static_cast<double*>(take(2 * nn * batch * 8));
   L.XTp = static_cast<double*>(take(2 * nn * batch * 8));
@@ -222,7 +232,7 @@ Layout carve(int n, int batch, void* ws) {
 size_t mixed_ws(int n, int batch) { return carve(n, batch, nullptr).bytes; }
 
 frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool hpd) {
   if (n > oz::K_MAX) return FROB_ERR_UNSUPPORTED;
   Layout L = carve(n, batch, ws);
   const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
@@ -234,11 +244,15 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   cudaMemsetAsync(L.nM2, 0, (size_t)batch * 8, st);
   cudaMemsetAsync(L.err, 0, 4, st);
   FROB_LAUNCH("mixed_conv_in", st,
-              conv_in_kernel<<<eg, 256, 0, st>>>(n, M, MatB<zf>{L.M32, n, nn}, L.Mp, L.nM2));
-  // X_0: Frobenius inversion in FP32 (also initialises info)
+              conv_in_kernel<<<eg, 256, 0, st>>>(n, M, MatB<zf>{L.M32, n, nn}, L.Mp, L.nM2, hpd ? 1 : 0));
+  // X_0: Frobenius inversion in FP32, with LU (Sec. 4.1) or, for Hermitian
+  // positive definite input, with Cholesky (Sec. 4.3); also initialises info
   frob_opts o32 = o;
   o32.prec = FROB_FP32;
-  frob_lu_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, o32, L.ws32, info, st);
+  if (hpd)
+    frob_chol_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, L.ws32, info, st);
+  else
+    frob_lu_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, o32, L.ws32, info, st);
   FROB_LAUNCH("mixed_conv_x", st, conv_x_kernel<<<eg, 256, 0, st>>>(n, MatB<const zf>{L.X32, n, nn}, L.Xp, L.XTp, batch));
   FROB_LAUNCH("mixed_init_skip", st, init_skip_kernel<<<(batch + 127) / 128, 128, 0, st>>>(info, L.skip, batch));
   launch_split(n, Kp, batch, S_RESID, L.Mp, L.Mdig, L.expM, L.skip, st);

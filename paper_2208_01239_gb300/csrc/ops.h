@@ -48,7 +48,7 @@ namespace mixed {
 // Mixed-precision Frobenius inversion with Newton-Schulz refinement (n <= 512).
 size_t mixed_ws(int n, int batch);
 frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
-                      cudaStream_t st);
+                      cudaStream_t st, bool hpd);
 }  // namespace mixed
 
 }  // namespace frob

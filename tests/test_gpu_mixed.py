@@ -64,6 +64,25 @@ def test_mixed_hpd_workload_kappa_1e4(F):
         assert metrics.forward_error(x[b], exact) <= 32 * 256 * kappa * U64
 
 
+@pytest.mark.parametrize("n", [5, 64, 129, 512])
+def test_mixed_hpd_route_vs_oracle(F, n):
+    """frob_inv_hpd in the mixed precisions: FP32 Cholesky-Frobenius start
+    (Sec. 4.3), FP64-accurate refinement; lower triangle read."""
+    batch = 3 if n < 512 else 8
+    ms, qs, lams = W.hpd(n, batch=batch, seed=8000 + n, return_parts=True)
+    bad = ms.copy()
+    bad[:, np.triu_indices(n, 1)[0], np.triu_indices(n, 1)[1]] = 9.0 + 9.0j  # upper triangle ignored
+    r = F.frob_inv_hpd(torch.from_numpy(bad).cuda(), prec="mixed_bf16")
+    x = r.x.cpu().numpy()
+    for b in range(batch):
+        exact = W.hpd_exact_inverse(qs[b], lams[b])
+        kappa = lams[b].max() / lams[b].min()
+        res = metrics.residual_fro(ms[b], x[b])
+        assert res <= 1e-13
+        assert metrics.forward_error(x[b], oracle.cplx_chol_inv(ms[b])) <= 32 * n * kappa * U64 + 4 * np.sqrt(n) * kappa * res
+        assert metrics.forward_error(x[b], exact) <= 32 * n * kappa * U64 + 4 * np.sqrt(n) * kappa * res
+
+
 def test_mixed_reports_failure_instead_of_wrong_result(F):
     """kappa(M) ~ 2e6 with S = (1 - s^2) I: the FP32 start cannot resolve S.
     Every matrix is either refined to the FP64 target or reported
