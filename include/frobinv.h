@@ -219,6 +219,31 @@ frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64
                              int64_t sg, void* gradM, int64_t ldr, int64_t sr, int prec, void* ws, size_t wsb,
                              void* stream);
 
+/*
+ * frob_inv_batched -- `batch` matrices of different orders in one call (no
+ * counterpart in the paper: the batched driver).  Each matrix M_i of order
+ * n_i is embedded as M_i (+) I in a bucket of order 32 ceil(n_i / 32) --
+ * (M (+) I)^{-1} = M^{-1} (+) I exactly -- and every bucket runs the uniform
+ * entry point selected by `op` (FROB_OP_INV, FROB_OP_INV_HPD, FROB_OP_CPLX_LU
+ * or FROB_OP_CPLX_CHOL) with `opts` (precision; the almost sure option is not
+ * supported here).  Results and info records are scattered back.
+ *
+ *   n_host, n_dev   the orders, on the host (to plan the launches) and on
+ *                   the device (identical contents)
+ *   M_dev, ldm_dev  device arrays of `batch` input pointers / leading dims
+ *   X_dev, ldx_dev  device arrays of `batch` output pointers / leading dims
+ *   ws, wsb         frob_inv_batched_workspace_bytes(op, batch, n_host, prec)
+ *   info            device array of `batch` frob_info records
+ * A call is a fixed launch sequence on `stream` (no allocation, no host
+ * synchronisation), so it may be captured into a CUDA graph after a first
+ * call on the device.
+ */
+size_t frob_inv_batched_workspace_bytes(int op, int batch, const int32_t* n_host, int prec);
+frob_status frob_inv_batched(int op, int batch, const int32_t* n_host, const int32_t* n_dev,
+                             const void* const* M_dev, const int64_t* ldm_dev, void* const* X_dev,
+                             const int64_t* ldx_dev, const frob_opts* opts, void* ws, size_t wsb, frob_info* info,
+                             void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 

@@ -99,6 +99,10 @@ def load() -> ctypes.CDLL:
         lib.frob_kernel_launches.restype = ctypes.c_uint64
         lib.frob_inv_adjoint.argtypes = common + [vp, i64, i64, i32, vp, sz, vp]
         lib.frob_inv_adjoint.restype = i32
+        lib.frob_inv_batched_workspace_bytes.argtypes = [i32, i32, vp, i32]
+        lib.frob_inv_batched_workspace_bytes.restype = sz
+        lib.frob_inv_batched.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
+        lib.frob_inv_batched.restype = i32
         lib.frob_gemm_tc.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, sz, vp,
                                      vp]
         lib.frob_gemm_tc.restype = i32
@@ -242,6 +246,68 @@ def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=Non
 def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
     """Complex Cholesky inversion (HPD baseline, lower triangle read)."""
     return _call("cplx_chol_inv", m, prec, None, out, ws, info, check)
+
+
+class Batched:
+    """A preallocated call of frob_inv_batched for a fixed list of orders.
+
+    ``inputs[i]`` / ``outputs[i]`` are (n_i, n_i) device tensors owned by the
+    plan; fill the inputs, then :meth:`run`.  :meth:`run` launches a fixed
+    kernel sequence on the current stream with no allocation, so it can be
+    captured with ``torch.cuda.graph`` after one eager call."""
+
+    def __init__(self, ns, op: str = "frob_inv", prec: str = "fp64", device="cuda", ns_tol: float = 1e-14,
+                 ns_max_iter: int = 8):
+        lib = load()
+        self.lib = lib
+        self.ns = [int(n) for n in ns]
+        self.batch = len(self.ns)
+        self.op = OP[op]
+        self.prec = prec
+        dt = _cdtype(prec)
+        dev = torch.device(device)
+        self.n_host = np.ascontiguousarray(np.array(self.ns, dtype=np.int32))
+        self.n_dev = torch.tensor(self.ns, dtype=torch.int32, device=dev)
+        self.inputs = [torch.zeros((n, n), dtype=dt, device=dev) for n in self.ns]
+        self.outputs = [torch.zeros((n, n), dtype=dt, device=dev) for n in self.ns]
+        self.m_ptrs = torch.tensor([t.data_ptr() for t in self.inputs], dtype=torch.int64, device=dev)
+        self.x_ptrs = torch.tensor([t.data_ptr() for t in self.outputs], dtype=torch.int64, device=dev)
+        self.lds = torch.tensor(self.ns, dtype=torch.int64, device=dev)
+        need = int(lib.frob_inv_batched_workspace_bytes(self.op, self.batch, self.n_host.ctypes.data, PREC[prec]))
+        if need == 0:
+            raise FrobError("frob_inv_batched: unsupported sizes / precision / operation", FROB_ERR_UNSUPPORTED)
+        self.ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        self.pad = (-self.ws.data_ptr()) % 256
+        self.info_dev = torch.zeros((self.batch, 32), dtype=torch.uint8, device=dev)
+        self.opts = _opts(prec)
+        self.opts.ns_tol = ns_tol
+        self.opts.ns_max_iter = ns_max_iter
+
+    def run(self):
+        st = self.lib.frob_inv_batched(self.op, self.batch, self.n_host.ctypes.data, self.n_dev.data_ptr(),
+                                       self.m_ptrs.data_ptr(), self.lds.data_ptr(), self.x_ptrs.data_ptr(),
+                                       self.lds.data_ptr(), ctypes.byref(self.opts), self.ws.data_ptr() + self.pad,
+                                       self.ws.numel() - self.pad, self.info_dev.data_ptr(),
+                                       torch.cuda.current_stream(self.ws.device).cuda_stream)
+        if st != FROB_OK:
+            raise FrobError(f"frob_inv_batched: {status_str(st)}", st)
+
+    def info(self) -> np.ndarray:
+        return parse_info(self.info_dev)
+
+
+def frob_inv_batched(mats, op: str = "frob_inv", prec: str = "fp64", check: bool = True):
+    """Invert a list of square complex matrices of different orders in one
+    call; returns (list of inverses, info records)."""
+    plan = Batched([m.shape[-1] for m in mats], op=op, prec=prec,
+                   device=mats[0].device if mats[0].is_cuda else "cuda")
+    for dst, src in zip(plan.inputs, mats):
+        dst.copy_(src)
+    plan.run()
+    info = plan.info()
+    if check:
+        check_info(info, "frob_inv_batched")
+    return plan.outputs, info
 
 
 def inv_adjoint(x: torch.Tensor, g: torch.Tensor, prec: str | None = None) -> torch.Tensor:
