@@ -158,6 +158,44 @@ def cpu_baseline(ms, budget_s=12.0):
                       f"OpenMP), {dt:.1f} s"}
 
 
+def measure_batched(frob, dev, steps, rank):
+    """1024 matrices with n uniform in [32, 512], A, B iid N(0, 1): the mixed
+    Frobenius form and the FP64 complex-LU baseline, both through
+    frob_inv_batched (one call per step, a fixed launch sequence)."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+    sizes, mats = W.uneven_batch(1024, 32, 512, seed=4 + 1000 * rank)
+    out = {"workload": "uneven_1024_n32-512_c128", "sum_n3": float(np.sum(np.asarray(sizes, dtype=np.float64) ** 3))}
+    for name, op, prec in (("frob_inv mixed_bf16", "frob_inv", "mixed_bf16"), ("cplx_lu_inv fp64", "cplx_lu_inv", "fp64")):
+        plan = frob.Batched(sizes, op=op, prec=prec, device=dev)
+        for dst, m in zip(plan.inputs, mats):
+            dst.copy_(torch.from_numpy(m))
+        plan.run()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        inf = plan.info()
+        worst = 0.0
+        for k in range(0, 1024, 128):
+            m = torch.from_numpy(mats[k]).to(dev)
+            x = plan.outputs[k]
+            r = m @ x - torch.eye(m.shape[0], dtype=m.dtype, device=dev)
+            worst = max(worst, (torch.linalg.norm(r) / (torch.linalg.norm(m) * torch.linalg.norm(x))).item())
+        out[name] = {"ms_per_step": ms, "inversions_per_s": 1024 / (ms * 1e-3),
+                     "status_ok": int((inf["status"] == 0).sum()), "residual_fro_max_sampled": worst}
+        del plan
+    a, b = out["frob_inv mixed_bf16"], out["cplx_lu_inv fp64"]
+    out["speedup_vs_cplx_lu"] = b["ms_per_step"] / a["ms_per_step"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +205,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true",
                     help="run the workload twice (one warm-up call) and exit: the command profiled by ncu")
+    ap.add_argument("--once-mixed", action="store_true",
+                    help="as --once, for the mixed-precision form")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 1024-matrix uneven workload")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="matrices per step for --once / --once-mixed (profiling a smaller case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -189,16 +232,17 @@ def main():
     fbuild.build()
     lib = frob.load()
 
-    ms, qs, lams = _gen_inputs(N_ORDER, BATCH, SEED + rank)
+    batch_n = args.batch if (args.once or args.once_mixed) else BATCH
+    ms, qs, lams = _gen_inputs(N_ORDER, batch_n, SEED + rank)
     m_host = torch.from_numpy(ms).pin_memory()
     m_dev = m_host.to(dev)
     x_dev = torch.empty_like(m_dev)
     x_host = torch.empty_like(m_host).pin_memory()
-    need = frob.workspace_bytes("frob_inv_hpd", N_ORDER, BATCH)
+    need = frob.workspace_bytes("frob_inv_hpd", N_ORDER, batch_n)
     ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
-    need_c = frob.workspace_bytes("cplx_chol_inv", N_ORDER, BATCH)
+    need_c = frob.workspace_bytes("cplx_chol_inv", N_ORDER, batch_n)
     ws_c = torch.empty(need_c + 256, dtype=torch.uint8, device=dev)
-    info = torch.zeros((BATCH, 32), dtype=torch.uint8, device=dev)
+    info = torch.zeros((batch_n, 32), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -209,6 +253,14 @@ def main():
         step()
         torch.cuda.synchronize(dev)
         frob.check_info(frob.parse_info(info), "frob_inv_hpd")
+        return 0
+    if args.once_mixed:
+        need_m = frob.workspace_bytes("frob_inv_hpd", N_ORDER, batch_n, "mixed_bf16")
+        ws_m = torch.empty(need_m + 256, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            frob.frob_inv_hpd(m_dev, prec="mixed_bf16", out=x_dev, ws=ws_m, info=info, check=False)
+        torch.cuda.synchronize(dev)
+        frob.check_info(frob.parse_info(info), "frob_inv_hpd mixed")
         return 0
 
     def step_baseline():
@@ -297,6 +349,8 @@ def main():
              "top_share": {k: round(v[1] / tot_m, 3) for k, v in
                            sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]}}
 
+    batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
+
     # end to end through the public API with host buffers
     def e2e_step():
         m_dev.copy_(m_host, non_blocking=True)
@@ -341,6 +395,7 @@ def main():
         "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                         "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)} for k, v in prof.items()},
         "mixed": mixed,
+        "batched_uneven": batched,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),
