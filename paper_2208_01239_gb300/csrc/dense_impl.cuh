@@ -25,7 +25,9 @@
 //                      search by warp-shuffle argmax.
 //   laswp_trsm_kernel  applies a panel's row swaps to the other columns and
 //                      forms U12 = L11^{-1} A12.
-//   potrf_panel_kernel Cholesky of one column panel (lower, A = L L^H).
+//   potrf_diag_kernel  Cholesky of a panel's diagonal block (lower,
+//                      A = L L^H), one warp per matrix.
+//   potrf_rows_kernel  the rows below it, L21 = A21 L11^{-H}, one thread per row.
 #pragma once
 
 #include <cstdint>
@@ -497,57 +499,76 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
   }
 }
 
-// Cholesky A = L L^H of the column panel [k0, k0+kb) over rows [k0, n),
-// lower triangle (grid: batch).  A non-positive or non-finite diagonal
-// reports FROB_ERR_NOT_HPD with bad_index = k + 1 + info_off.
+// Cholesky of the kb x kb diagonal block of the panel [k0, k0+kb) (lower,
+// A11 = L11 L11^H), one warp per matrix (grid: batch).  A non-positive or
+// non-finite diagonal reports FROB_ERR_NOT_HPD with bad_index =
+// k + 1 + info_off and continues with a unit pivot.
 template <typename T>
-__global__ void __launch_bounds__(PANEL_THREADS) potrf_panel_kernel(int n, int k0, int kb, MatB<T> A,
-                                                                     frob_info* info, int info_off, int staged) {
+__global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int k0, int kb, MatB<T> A, frob_info* info,
+                                                         int info_off) {
   using K = typename real_of<T>::type;
   const int b = blockIdx.x;
-  const int t = threadIdx.x;
-  const int m = n - k0;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ K s_rinv;
+  const int lane = threadIdx.x;
+  __shared__ T D[PANEL_MAX][PANEL_MAX + 1];
   T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
-  T* P;
-  int64_t ps;
-  if (staged) {
-    P = reinterpret_cast<T*>(smraw);
-    ps = kb;
-    for (int e = t; e < m * kb; e += PANEL_THREADS) P[e] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
-    __syncthreads();
-  } else {
-    P = g;
-    ps = A.ld;
-  }
+  for (int r = 0; r < kb; ++r)
+    if (lane <= r) D[r][lane] = g[(int64_t)r * A.ld + lane];
+  __syncwarp();
+  int fail = -1;
   for (int j = 0; j < kb; ++j) {
-    if (t == 0) {
-      K d = real_(P[(int64_t)j * ps + j]);
-      bool ok = d > (K)0 && d < (K)INFINITY;
-      if (!ok) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + j + 1);
-      K l = ok ? sqrt(d) : (K)1;
-      P[(int64_t)j * ps + j] = from_real<T>(l);
-      s_rinv = (K)1 / l;
+    const K d = real_(D[j][j]);
+    const bool ok = d > (K)0 && d < (K)INFINITY;
+    if (!ok && fail < 0) fail = j;
+    const K l = ok ? sqrt(d) : (K)1;
+    __syncwarp();
+    if (lane == j) D[j][j] = from_real<T>(l);
+    if (lane > j && lane < kb) D[lane][j] = mul_(D[lane][j], from_real<T>((K)1 / l));
+    __syncwarp();
+    if (lane > j && lane < kb) {
+      const T lij = neg_(D[lane][j]);
+      for (int c = j + 1; c <= lane; ++c) mac(D[lane][c], lij, conj_(D[c][j]));
     }
-    __syncthreads();
-    const K rinv = s_rinv;
-    for (int r = j + 1 + t; r < m; r += PANEL_THREADS) {
-      T v = P[(int64_t)r * ps + j];
-      P[(int64_t)r * ps + j] = mul_(v, from_real<T>(rinv));
-    }
-    __syncthreads();
-    for (int r = j + 1 + t; r < m; r += PANEL_THREADS) {
-      T l = neg_(P[(int64_t)r * ps + j]);
-      T* row = P + (int64_t)r * ps;
-      int cmax = r < kb - 1 ? r : kb - 1;
-      for (int c = j + 1; c <= cmax; ++c) mac(row[c], l, conj_(P[(int64_t)c * ps + j]));
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  if (staged) {
-    for (int e = t; e < m * kb; e += PANEL_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[e];
+  if (fail >= 0 && lane == 0) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + fail + 1);
+  for (int r = 0; r < kb; ++r)
+    if (lane <= r) g[(int64_t)r * A.ld + lane] = D[r][lane];
+}
+
+// Rows below the diagonal block: L21 = A21 L11^{-H}, i.e. each row x solves
+// x L11^H = a (grid: row blocks of 128 x batch, one thread per row).
+template <typename T>
+__global__ void __launch_bounds__(128) potrf_rows_kernel(int n, int k0, int kb, MatB<T> A) {
+  using K = typename real_of<T>::type;
+  const int b = blockIdx.y;
+  __shared__ T L[PANEL_MAX][PANEL_MAX + 1];
+  __shared__ K dinv[PANEL_MAX];
+  T* Ab = A.at(b);
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    L[r][c] = (c <= r) ? Ab[(int64_t)(k0 + r) * A.ld + k0 + c] : zero_v<T>();
   }
+  __syncthreads();
+  if (threadIdx.x < kb) dinv[threadIdx.x] = (K)1 / real_(L[threadIdx.x][threadIdx.x]);
+  __syncthreads();
+  const int row = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  T* a = Ab + (int64_t)row * A.ld + k0;
+  T x[PANEL_MAX];
+#pragma unroll
+  for (int j = 0; j < PANEL_MAX; ++j) x[j] = j < kb ? a[j] : zero_v<T>();
+#pragma unroll
+  for (int j = 0; j < PANEL_MAX; ++j) {
+    if (j < kb) {
+      T s = x[j];
+#pragma unroll
+      for (int i = 0; i < j; ++i) mac(s, neg_(x[i]), conj_(L[j][i]));
+      x[j] = mul_(s, from_real<T>(dinv[j]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PANEL_MAX; ++j)
+    if (j < kb) a[j] = x[j];
 }
 
 }  // namespace frob

@@ -109,21 +109,32 @@ __global__ void conv_out_kernel(int n, const double* Xp, MatB<zd> X, int batch) 
   X.at(b)[(int64_t)i * X.ld + j] = zd{Xp[(int64_t)b * nn + e], Xp[((int64_t)batch + b) * nn + e]};
 }
 
-// ||X||_F^2 per matrix into nX2, and zero the residual accumulators
-__global__ void xnorm_kernel(int n, const double* Xp, double* nX2, double* rn2, int batch, const int* skip) {
+// ||X||_F^2 per matrix into nX2.  FP32 is ample for the norm in a relative
+// residual and keeps the work off the FP64 pipe; each block reduces 16
+// elements per thread before a single atomic.
+constexpr int XN_PER_THREAD = 16;
+__global__ void xnorm_kernel(int n, const double* Xp, double* nX2, int batch, const int* skip) {
   const int b = blockIdx.z;
   if (skip[b]) return;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nn = (int64_t)n * n;
-  // FP32 is ample for the norm in a relative residual, and keeps the work
-  // off the FP64 pipe
+  const int64_t e0 = (int64_t)blockIdx.x * blockDim.x * XN_PER_THREAD + threadIdx.x;
   float ss = 0.f;
-  if (e < nn) {
-    const float a = (float)Xp[(int64_t)b * nn + e], c = (float)Xp[((int64_t)batch + b) * nn + e];
-    ss = a * a + c * c;
+  for (int k = 0; k < XN_PER_THREAD; ++k) {
+    const int64_t e = e0 + (int64_t)k * blockDim.x;
+    if (e < nn) {
+      const float a = (float)Xp[(int64_t)b * nn + e], c = (float)Xp[((int64_t)batch + b) * nn + e];
+      ss = fmaf(a, a, fmaf(c, c, ss));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if ((threadIdx.x & 31) == 0 && ss != 0.f) atomicAdd(nX2 + b, (double)ss);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && v != 0.f) atomicAdd(nX2 + b, (double)v);
+  }
 }
 
 __global__ void zero_kernel(double* a, double* c, int batch, const int* skip) {
@@ -283,7 +294,8 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
 
   for (int it = 0; it <= max_iter; ++it) {
     FROB_LAUNCH("mixed_zero", st, zero_kernel<<<(batch + 127) / 128, 128, 0, st>>>(L.rn2, L.nX2, batch, L.skip));
-    FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<eg, 256, 0, st>>>(n, L.Xp, L.nX2, L.rn2, batch, L.skip));
+    const dim3 xg((unsigned)((nn + 256 * XN_PER_THREAD - 1) / (256 * XN_PER_THREAD)), 1, batch);
+    FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<xg, 256, 0, st>>>(n, L.Xp, L.nX2, batch, L.skip));
     launch_split(n, Kp, batch, S_RESID, L.XTp, L.Bdig, L.expB, L.skip, st);
     launch_cgemm<oz::RESID>(mapM, mapXT7, ra, st);                                   // R = I - M X
     FROB_LAUNCH("mixed_check", st,

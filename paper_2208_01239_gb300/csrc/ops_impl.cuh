@@ -179,7 +179,6 @@ template <typename T> inline void panel_smem_attr() {
   static bool done = false;
   if (!done) {
     cudaFuncSetAttribute(getrf_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX);
-    cudaFuncSetAttribute(potrf_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX);
     cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)laswp_trsm_smem<T>());
     done = true;
@@ -194,11 +193,6 @@ template <typename T> inline const char* laswp_name() {
   static const std::string s = std::string("laswp_trsm<") + type_tag<T>() + ">";
   return s.c_str();
 }
-template <typename T> inline const char* potrf_panel_name() {
-  static const std::string s = std::string("potrf_panel<") + type_tag<T>() + ">";
-  return s.c_str();
-}
-
 // Blocked right-looking LU with partial pivoting (P A = L U, in place).
 template <typename T>
 inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st) {
@@ -222,18 +216,29 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
   }
 }
 
-// Blocked right-looking Cholesky (A = L L^H, lower triangle, in place).
+// Blocked right-looking Cholesky (A = L L^H, lower triangle, in place): per
+// 32-wide panel, the diagonal block by one warp per matrix, the rows below it
+// by one thread per row across the grid, then the trailing update of the
+// lower tiles.
+template <typename T> inline const char* potrf_diag_name() {
+  static const std::string s = std::string("potrf_diag<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+template <typename T> inline const char* potrf_rows_name() {
+  static const std::string s = std::string("potrf_rows<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+
 template <typename T>
 inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cudaStream_t st) {
-  panel_smem_attr<T>();
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
-    const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
-    const int staged = bytes <= PANEL_SMEM_MAX;
-    FROB_LAUNCH(potrf_panel_name<T>(), st, potrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, info, info_off, staged));
+    FROB_LAUNCH(potrf_diag_name<T>(), st, potrf_diag_kernel<T><<<batch, 32, 0, st>>>(n, k0, kb, A, info, info_off));
     const int r = k0 + kb;
     if (r < n) {
+      FROB_LAUNCH(potrf_rows_name<T>(), st,
+                  potrf_rows_kernel<T><<<dim3((n - r + 127) / 128, batch), 128, 0, st>>>(n, k0, kb, A));
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
       MatB<T> A22 = A.sub(r, r);
       gemm_launch<T, OP_N, OP_C>(n - r, n - r, kb, batch, L21, L21, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),

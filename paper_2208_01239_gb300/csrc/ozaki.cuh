@@ -22,9 +22,11 @@
 // Complex product C = A B with A = Ar + i Ai, B = Br + i Bi:
 //   Re C = Ar Br - Ai Bi,  Im C = Ar Bi + Ai Br;
 // each output part is two real terms.  The kernel computes one 128 x 64 tile
-// of one part: for each term, for each digit s of the A operand the 128-row
-// digit slice stays resident in shared memory while the digit slices of B
-// stream through a TMA ring; tcgen05.mma accumulates into the group
+// of one part: for each term, for each digit s of the A operand, for each
+// 256-wide K chunk, the 128 x 256 chunk of the digit slice stays resident in
+// shared memory (two chunk buffers, so that the next chunk loads while the
+// current one is used) while the matching K chunks of the digit slices of B
+// stream through a 12-stage TMA ring; tcgen05.mma accumulates into the group
 // accumulators in TMEM; after each term the epilogue warps add the groups,
 // scaled by their powers of two and the row / column exponents, into a
 // float-float (hi + lo) accumulator with error-free two-sums.  The final
@@ -51,9 +53,11 @@ constexpr int S_MAX = 7;
 constexpr int BN = 64;        // output tile columns
 constexpr int KB = 64;        // BF16 elements per k-block (one 128-byte row)
 constexpr int K_MAX = 512;    // largest inner dimension with exact FP32 accumulation
-constexpr int A_RES_BYTES = tc::BM * K_MAX * 2;  // resident A digit slice (128 x 512 BF16)
-constexpr int B_STAGE_BYTES = BN * KB * 2;        // 8 KB
-constexpr int B_STAGES = 6;
+constexpr int A_CHUNK_KB = 4;                              // k-blocks per resident A chunk
+constexpr int A_CHUNK_BYTES = tc::BM * KB * 2 * A_CHUNK_KB;  // 64 KB: 128 rows x 256 K
+constexpr int A_RES_BYTES = 2 * A_CHUNK_BYTES;               // double-buffered
+constexpr int B_STAGE_BYTES = BN * KB * 2;                  // 8 KB
+constexpr int B_STAGES = 12;
 constexpr int NUM_GROUPS = 8;
 constexpr int THREADS = 192;
 constexpr int SMEM_BYTES = A_RES_BYTES + B_STAGES * B_STAGE_BYTES + 1024 + 512 + 4 * BN * 4;
@@ -189,9 +193,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(b_ring + B_STAGES * B_STAGE_BYTES);
   uint64_t* b_full = bars;
   uint64_t* b_empty = bars + B_STAGES;
-  uint64_t* a_full = bars + 2 * B_STAGES;
-  uint64_t* a_empty = a_full + 1;
-  uint64_t* term_done = a_empty + 1;
+  uint64_t* a_full = bars + 2 * B_STAGES;  // [2]
+  uint64_t* a_empty = a_full + 2;          // [2]
+  uint64_t* term_done = a_empty + 2;
   uint64_t* drained = term_done + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
 
@@ -212,8 +216,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
     }
-    mbar_init(a_full, 1);
-    mbar_init(a_empty, 1);
+    mbar_init(&a_full[0], 1);
+    mbar_init(&a_full[1], 1);
+    mbar_init(&a_empty[0], 1);
+    mbar_init(&a_empty[1], 1);
     mbar_init(term_done, 1);
     mbar_init(drained, 4);
     fence_mbar_init();
@@ -230,25 +236,33 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (!skip) {
     if (warp == 0 && lane == 0) {
       // ---------------- producer
+      const int nch = (nkb + A_CHUNK_KB - 1) / A_CHUNK_KB;
       int bi = 0;   // B stage fill counter
-      int ai = 0;   // A fill counter
+      int ai = 0;   // A chunk fill counter
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
         const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
         for (int s = 1; s <= S && ok; ++s) {
-          if (ai > 0 && !mbar_wait(a_empty, (ai - 1) & 1)) { ok = false; break; }
-          mbar_arrive_expect_tx(a_full, (uint32_t)(nkb * BM * KB * 2));
           const int za = (ap * S + (s - 1)) * batch + b;
-          for (int kb = 0; kb < nkb; ++kb) tma_load_3d(a_res + kb * (BM * KB * 2), &mapA, a_full, kb * KB, m0, za);
-          ++ai;
-          for (int t = 1; t <= S + 1 - s && ok; ++t) {
-            const int zb = (bp * S + (t - 1)) * batch + b;
-            for (int kb = 0; kb < nkb; ++kb) {
-              const int st = bi % B_STAGES;
-              if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
-              mbar_arrive_expect_tx(&b_full[st], B_STAGE_BYTES);
-              tma_load_3d(b_ring + st * B_STAGE_BYTES, &mapB, &b_full[st], kb * KB, n0, zb);
-              ++bi;
+          for (int ch = 0; ch < nch && ok; ++ch) {
+            const int kb0 = ch * A_CHUNK_KB;
+            const int kb1 = (kb0 + A_CHUNK_KB < nkb) ? kb0 + A_CHUNK_KB : nkb;
+            const int slot = ai & 1;
+            if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
+            mbar_arrive_expect_tx(&a_full[slot], (uint32_t)((kb1 - kb0) * BM * KB * 2));
+            unsigned char* abuf = a_res + slot * A_CHUNK_BYTES;
+            for (int kb = kb0; kb < kb1; ++kb)
+              tma_load_3d(abuf + (kb - kb0) * (BM * KB * 2), &mapA, &a_full[slot], kb * KB, m0, za);
+            ++ai;
+            for (int t = 1; t <= S + 1 - s && ok; ++t) {
+              const int zb = (bp * S + (t - 1)) * batch + b;
+              for (int kb = kb0; kb < kb1; ++kb) {
+                const int st = bi % B_STAGES;
+                if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
+                mbar_arrive_expect_tx(&b_full[st], B_STAGE_BYTES);
+                tma_load_3d(b_ring + st * B_STAGE_BYTES, &mapB, &b_full[st], kb * KB, n0, zb);
+                ++bi;
+              }
             }
           }
         }
@@ -257,6 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t IDESC = instr_desc<0, BN>();
+      const int nch = (nkb + A_CHUNK_KB - 1) / A_CHUNK_KB;
       int bi = 0, ai = 0;
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
@@ -264,31 +279,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_after();
         uint32_t started = 0;
         for (int s = 1; s <= S && ok; ++s) {
-          if (!mbar_wait(a_full, ai & 1)) { ok = false; break; }
-          ++ai;
-          tc_fence_after();
-          const uint32_t sa = smem_u32(a_res);
-          for (int t = 1; t <= S + 1 - s && ok; ++t) {
-            const int g = group_of(s, t);
-            const uint32_t dt = tmem + (uint32_t)(g * BN);
-            for (int kb = 0; kb < nkb; ++kb) {
-              const int st = bi % B_STAGES;
-              if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
+          for (int ch = 0; ch < nch && ok; ++ch) {
+            const int kb0 = ch * A_CHUNK_KB;
+            const int kb1 = (kb0 + A_CHUNK_KB < nkb) ? kb0 + A_CHUNK_KB : nkb;
+            const int slot = ai & 1;
+            if (!mbar_wait(&a_full[slot], (ai >> 1) & 1)) { ok = false; break; }
+            ++ai;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(a_res + slot * A_CHUNK_BYTES);
+            for (int t = 1; t <= S + 1 - s && ok; ++t) {
+              const int g = group_of(s, t);
+              const uint32_t dt = tmem + (uint32_t)(g * BN);
+              for (int kb = kb0; kb < kb1; ++kb) {
+                const int st = bi % B_STAGES;
+                if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
 #pragma unroll
-              for (int kk = 0; kk < KB / 16; ++kk) {
-                const uint64_t ad = sw128_desc(sa + kb * (BM * KB * 2) + kk * 32);
-                const uint64_t bd = sw128_desc(sb + kk * 32);
-                const uint32_t acc = ((started >> g) & 1u) ? 1u : 0u;
-                mma<0>(dt, ad, bd, IDESC, acc);
-                started |= 1u << g;
+                for (int kk = 0; kk < KB / 16; ++kk) {
+                  const uint64_t ad = sw128_desc(sa + (kb - kb0) * (BM * KB * 2) + kk * 32);
+                  const uint64_t bd = sw128_desc(sb + kk * 32);
+                  const uint32_t acc = ((started >> g) & 1u) ? 1u : 0u;
+                  mma<0>(dt, ad, bd, IDESC, acc);
+                  started |= 1u << g;
+                }
+                mma_commit(&b_empty[st]);
+                ++bi;
               }
-              mma_commit(&b_empty[st]);
-              ++bi;
             }
+            mma_commit(&a_empty[slot]);  // chunk buffer free once these MMAs complete
           }
-          mma_commit(a_empty);  // A slice free once these MMAs complete
         }
         mma_commit(term_done);  // phase `term` of term_done
       }
