@@ -26,6 +26,8 @@ of Dai, Lim and Ye, "Complex matrix inversion via real matrix inversions":
 * :func:`inv2x2`, :func:`adjugate_inv` -- closed forms used as pins.
 * :func:`inv_adjoint`   -- -X^H G X^H, the gradient of a real loss through
                            X = M^{-1} (from d(M^{-1}) = -M^{-1} dM M^{-1}).
+* :func:`frob_solve`    -- Algorithm "Linear system with Frobenius
+                           inversion" (Sec. 3), several right-hand sides.
 * :func:`sign_newton`   -- Newton's iteration for the matrix sign function
                            (Sec. 5.3, eq. "iter"), fixed step count.
 
@@ -120,6 +122,7 @@ class Oracle:
             "orc_num_threads": [],
             "orc_inv_adjoint": [i, zp, zp, zp],
             "orc_sign_newton": [i, zp, i, zp],
+            "orc_frob_solve": [i, i, zp, zp, zp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -206,6 +209,17 @@ class Oracle:
         _check("inv_adjoint", self.lib.orc_inv_adjoint(n, _ptr(x), _ptr(g), _ptr(out)))
         return out
 
+    def frob_solve(self, m, rhs) -> np.ndarray:
+        """Solve M X = RHS (RHS n x nrhs complex) by Algorithm "Linear system
+        with Frobenius inversion" (Sec. 3)."""
+        m, n = _prep(m)
+        rhs = np.ascontiguousarray(np.asarray(rhs, dtype=np.complex128))
+        vec = rhs.ndim == 1
+        r2 = rhs.reshape(n, -1).copy()
+        x = np.empty_like(r2)
+        _check("frob_solve", self.lib.orc_frob_solve(n, r2.shape[1], _ptr(m), _ptr(r2), _ptr(x)))
+        return x[:, 0] if vec else x
+
     def sign_newton(self, m, iters: int) -> np.ndarray:
         """`iters` Newton steps X <- (X + X^{-1})/2 from X = M (Sec. 5.3)."""
         m, n = _prep(m)
@@ -264,6 +278,10 @@ def inv_adjoint(x, g):
 
 def sign_newton(m, iters: int):
     return load().sign_newton(m, iters)
+
+
+def frob_solve(m, rhs):
+    return load().frob_solve(m, rhs)
 
 
 from . import metrics  # noqa: E402,F401

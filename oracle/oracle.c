@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORC_MUTANT plants one deliberate mistake (k = 1..9) so that a test can check
+/* ORC_MUTANT plants one deliberate mistake (k = 1..10) so that a test can check
  * that the pins catch it.  Product builds of the oracle use ORC_MUTANT = 0. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -613,6 +613,90 @@ int orc_sign_newton(int n, const zc *m, int iters, zc *out)
     }
     free(xi);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm "Linear system with Frobenius inversion" (Sec. 3) for nrhs      */
+/* right-hand sides c + i d (n x nrhs, row-major complex):                   */
+/* A = P1^T L1 U1; L1 U1 X1 = P1 B; X2 = A + B X1; X2 = P2^T L2 U2;           */
+/* L2 U2 [x1, y1] = P2 [c, d]; L1 U1 [x2, y2] = P1 B [y1, x1];               */
+/* x = x1 + x2, y = y1 - y2.                                                  */
+/* The printed last step reads y = y2 - y1; by eq. (1.1) the imaginary part  */
+/* of M^{-1}(c + i d) is S^{-1} d - A^{-1} B S^{-1} c = y1 - y2, which the     */
+/* pins confirm.                                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Solve L U X = P C for a real n x m right-hand side (row-major, ld m). */
+static void dlu_solve_rhs(int n, int m, const double *lu, const int *piv, double *c)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = piv[k];
+        if (p != k)
+            for (int j = 0; j < m; ++j) { double t = c[(size_t)k * m + j]; c[(size_t)k * m + j] = c[(size_t)p * m + j]; c[(size_t)p * m + j] = t; }
+    }
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double s = c[(size_t)i * m + j];
+            for (int k = 0; k < i; ++k) s -= lu[IDX(i, k)] * c[(size_t)k * m + j];
+            c[(size_t)i * m + j] = s;
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = c[(size_t)i * m + j];
+            for (int k = i + 1; k < n; ++k) s -= lu[IDX(i, k)] * c[(size_t)k * m + j];
+            c[(size_t)i * m + j] = s / lu[IDX(i, i)];
+        }
+    }
+}
+
+int orc_frob_solve(int n, int nrhs, const zc *m, const zc *rhs, zc *x)
+{
+    if (n < 1 || nrhs < 1) return -2;
+    size_t nn = (size_t)n * n, nm = (size_t)n * nrhs;
+    double *w = malloc(sizeof(double) * (nn * 5 + nm * 4));
+    int *piv1 = malloc(sizeof(int) * (size_t)n), *piv2 = malloc(sizeof(int) * (size_t)n);
+    if (!w || !piv1 || !piv2) { free(w); free(piv1); free(piv2); return -1; }
+    double *A = w, *B = w + nn, *LU1 = w + 2 * nn, *X1 = w + 3 * nn, *X2 = w + 4 * nn;
+    double *CD = w + 5 * nn;           /* [c | d], n x 2 nrhs, becomes [x1 | y1] */
+    double *T = CD + 2 * nm;           /* B [y1 | x1], becomes [x2 | y2] */
+    split_planes(n, m, A, B);
+    memcpy(LU1, A, sizeof(double) * nn);
+    int info = dgetrf_plain(n, LU1, piv1);                        /* step 1 */
+    if (info) goto done;
+    memcpy(X1, B, sizeof(double) * nn);
+    dlu_solve_cols(n, LU1, piv1, X1);                             /* step 2 */
+    dgemm_plain(n, B, X1, A, X2);                                 /* step 3 */
+    info = dgetrf_plain(n, X2, piv2);                             /* step 4 */
+    if (info) { info += n; goto done; }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < nrhs; ++j) {
+            CD[(size_t)i * 2 * nrhs + j] = creal(rhs[(size_t)i * nrhs + j]);
+            CD[(size_t)i * 2 * nrhs + nrhs + j] = cimag(rhs[(size_t)i * nrhs + j]);
+        }
+    dlu_solve_rhs(n, 2 * nrhs, X2, piv2, CD);                      /* step 5 */
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)                                   /* step 6: B [y1, x1] */
+        for (int j = 0; j < nrhs; ++j) {
+            double sy = 0.0, sx = 0.0;
+            for (int k = 0; k < n; ++k) {
+                sy += B[IDX(i, k)] * CD[(size_t)k * 2 * nrhs + nrhs + j];
+                sx += B[IDX(i, k)] * CD[(size_t)k * 2 * nrhs + j];
+            }
+            T[(size_t)i * 2 * nrhs + j] = sy;
+            T[(size_t)i * 2 * nrhs + nrhs + j] = sx;
+        }
+    dlu_solve_rhs(n, 2 * nrhs, LU1, piv1, T);
+    for (int i = 0; i < n; ++i)                                   /* step 7 */
+        for (int j = 0; j < nrhs; ++j) {
+            double x1 = CD[(size_t)i * 2 * nrhs + j], y1 = CD[(size_t)i * 2 * nrhs + nrhs + j];
+            double x2 = T[(size_t)i * 2 * nrhs + j], y2 = T[(size_t)i * 2 * nrhs + nrhs + j];
+            x[(size_t)i * nrhs + j] = (x1 + x2) + I * (ORC_MUTANT == 10 ? y2 - y1 : y1 - y2);
+        }
+done:
+    free(w);
+    free(piv1);
+    free(piv2);
+    return info;
 }
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */

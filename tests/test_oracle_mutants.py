@@ -24,6 +24,7 @@ MUTANTS = {
     7: "column swaps in forward order (left LU inverse)",
     8: "X^T instead of X^H in the adjoint",
     9: "X + X^{-1} instead of (X + X^{-1})/2 in the sign iteration",
+    10: "y = y2 - y1 (the printed sign) in the Frobenius linear solve",
 }
 
 
@@ -81,6 +82,11 @@ def _pin_failures(o) -> list:
     sref = z @ np.diag(np.sign(re)) @ np.linalg.inv(z)
     if np.abs(o.sign_newton(x, 40) - sref).max() > 1e-9 * np.abs(sref).max():
         fails.append("sign closed form")
+    # Frobenius linear solve against LAPACK
+    m = g.standard_normal((9, 9)) + 1j * g.standard_normal((9, 9))
+    rhs = g.standard_normal((9, 2)) + 1j * g.standard_normal((9, 2))
+    if metrics.forward_error(o.frob_solve(m, rhs), np.linalg.solve(m, rhs)) > 1e-10:
+        fails.append("frob_solve lapack")
     return fails
 
 
