@@ -244,6 +244,29 @@ frob_status frob_inv_batched(int op, int batch, const int32_t* n_host, const int
                              const int64_t* ldx_dev, const frob_opts* opts, void* ws, size_t wsb, frob_info* info,
                              void* stream);
 
+/*
+ * frob_solve -- solve (A + iB)(X + iY) = C + iD for nrhs right-hand sides
+ * without forming the inverse (Sec. 3, Algorithm "Linear system with
+ * Frobenius inversion"): A = P1^T L1 U1; X1 = A^{-1} B by two triangular
+ * solves; S = A + B X1; S = P2^T L2 U2; [x1, y1] = S^{-1} [C, D];
+ * [x2, y2] = A^{-1} B [y1, x1]; X = x1 + x2, Y = y1 - y2 (the imaginary part
+ * of M^{-1}(C + iD) by eq. (1.1); the printed last step has the opposite
+ * sign).  M: n x n strided batch; B (right-hand sides) and X (solutions):
+ * n x nrhs strided batches (row-major, complex, ld >= nrhs).  prec
+ * FROB_FP64 (complex128) or FROB_FP32 (complex64).  FROB_ERR_SINGULAR per
+ * matrix as for frob_inv.  Workspace: frob_solve_workspace_bytes(0, ...).
+ *
+ * cplx_lu_solve -- the baseline: M = P^T L U in complex arithmetic, then
+ * L U X = P B.  Workspace: frob_solve_workspace_bytes(1, ...).
+ */
+size_t frob_solve_workspace_bytes(int op, int n, int nrhs, int batch, int prec);
+frob_status frob_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B, int64_t ldb,
+                       int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb, frob_info* info,
+                       void* stream);
+frob_status cplx_lu_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B,
+                          int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
+                          frob_info* info, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 

@@ -242,6 +242,64 @@ frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64
   return launched();
 }
 
+size_t frob_solve_workspace_bytes(int op, int n, int nrhs, int batch, int prec) {
+  if (n < 1 || nrhs < 1 || batch < 1 || !valid_prec(prec)) return 0;
+  const bool f32 = prec == FROB_FP32;
+  if (op == 0) return f32 ? frob_solve_ws<float>(n, nrhs, batch, nullptr, nullptr)
+                          : frob_solve_ws<double>(n, nrhs, batch, nullptr, nullptr);
+  if (op == 1) return f32 ? cplx_solve_ws<zf>(n, nrhs, batch) : cplx_solve_ws<zd>(n, nrhs, batch);
+  return 0;
+}
+
+static frob_status solve_common(int op, int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm,
+                                const void* B, int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec,
+                                void* ws, size_t wsb, frob_info* info, void* stream) {
+  if (n < 1 || nrhs < 1 || batch < 1 || batch > 65535 || !M || !B || !X || !info) return FROB_ERR_ARG;
+  if (ldm < n || ldb < nrhs || ldx < nrhs) return FROB_ERR_ARG;
+  if (batch > 1 && (sm < ldm * (int64_t)n || sb < ldb * (int64_t)n || sx < ldx * (int64_t)n)) return FROB_ERR_ARG;
+  if (!valid_prec(prec)) return FROB_ERR_UNSUPPORTED;
+  const size_t eb = elem_bytes(prec);
+  auto span = [&](int64_t ld, int64_t s, int cols) { return (size_t)(((int64_t)(batch - 1) * s + (int64_t)(n - 1) * ld + cols) * (int64_t)eb); };
+  auto ovl = [&](const void* a, size_t la, const void* c, size_t lc) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pc = static_cast<const char*>(c);
+    return pa < pc + lc && pc < pa + la;
+  };
+  if (ovl(X, span(ldx, sx, nrhs), M, span(ldm, sm, n)) || ovl(X, span(ldx, sx, nrhs), B, span(ldb, sb, nrhs)))
+    return FROB_ERR_ARG;
+  const size_t need = frob_solve_workspace_bytes(op, n, nrhs, batch, prec);
+  if (!ws || wsb < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return FROB_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (op == 0) {
+    if (prec == FROB_FP32)
+      frob_solve_run<float>(n, nrhs, batch, in_view<zf>(M, ldm, sm), in_view<zf>(B, ldb, sb), out_view<zf>(X, ldx, sx),
+                            ws, info, st);
+    else
+      frob_solve_run<double>(n, nrhs, batch, in_view<zd>(M, ldm, sm), in_view<zd>(B, ldb, sb),
+                             out_view<zd>(X, ldx, sx), ws, info, st);
+  } else {
+    if (prec == FROB_FP32)
+      cplx_solve_run<zf>(n, nrhs, batch, in_view<zf>(M, ldm, sm), in_view<zf>(B, ldb, sb), out_view<zf>(X, ldx, sx),
+                         ws, info, st);
+    else
+      cplx_solve_run<zd>(n, nrhs, batch, in_view<zd>(M, ldm, sm), in_view<zd>(B, ldb, sb), out_view<zd>(X, ldx, sx),
+                         ws, info, st);
+  }
+  return launched();
+}
+
+frob_status frob_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B, int64_t ldb,
+                       int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb, frob_info* info,
+                       void* stream) {
+  return solve_common(0, n, nrhs, batch, M, ldm, sm, B, ldb, sb, X, ldx, sx, prec, ws, wsb, info, stream);
+}
+
+frob_status cplx_lu_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B,
+                          int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
+                          frob_info* info, void* stream) {
+  return solve_common(1, n, nrhs, batch, M, ldm, sm, B, ldb, sb, X, ldx, sx, prec, ws, wsb, info, stream);
+}
+
 const char* frob_status_str(int status) {
   switch (status) {
     case FROB_OK: return "FROB_OK";

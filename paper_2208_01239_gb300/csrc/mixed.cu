@@ -28,6 +28,7 @@ namespace frob {
 namespace mixed {
 
 constexpr int S_RESID = 7;
+constexpr int S_RESID_FIRST = 5;  // the first residual's error adds to ||R_0||^2: 2^-36 suffices
 constexpr int S_CORR = 4;
 
 namespace {
@@ -280,6 +281,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   ra.Kp = Kp;
   ra.batch = batch;
   ra.S = S_RESID;
+  ra.Su = S_RESID;
   ra.expA = L.expM;
   ra.expB = L.expB;
   ra.outR = L.RTp;
@@ -288,6 +290,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   ra.err = L.err;
   oz::OzArgs ca = ra;
   ca.S = S_CORR;
+  ca.Su = S_CORR;
   ca.expA = L.expX;
   ca.X = L.Xp;
   ca.XT = L.XTp;
@@ -297,6 +300,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
     const dim3 xg((unsigned)((nn + 256 * XN_PER_THREAD - 1) / (256 * XN_PER_THREAD)), 1, batch);
     FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<xg, 256, 0, st>>>(n, L.Xp, L.nX2, batch, L.skip));
     launch_split(n, Kp, batch, S_RESID, L.XTp, L.Bdig, L.expB, L.skip, st);
+    ra.Su = it == 0 ? S_RESID_FIRST : S_RESID;
     launch_cgemm<oz::RESID>(mapM, mapXT7, ra, st);                                   // R = I - M X
     FROB_LAUNCH("mixed_check", st,
                 check_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, it, it == max_iter, tol, L.rn2, L.nM2, L.nX2,

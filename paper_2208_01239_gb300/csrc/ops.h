@@ -39,6 +39,17 @@ template <typename C> size_t cplx_chol_ws(int n, int batch, void* ws, CPlanes<C>
 template <typename C> void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info,
                                          cudaStream_t st);
 
+template <typename R> struct SolvePlanes;
+template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlanes<R>* out, void* ws);
+template <typename R>
+void frob_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::type> M,
+                    MatB<const typename cplx_of<R>::type> Bc, MatB<typename cplx_of<R>::type> X, void* ws,
+                    frob_info* info, cudaStream_t st);
+template <typename C> size_t cplx_solve_ws(int n, int nrhs, int batch);
+template <typename C>
+void cplx_solve_run(int n, int nrhs, int batch, MatB<const C> M, MatB<const C> Bc, MatB<C> X, void* ws,
+                    frob_info* info, cudaStream_t st);
+
 template <typename R> size_t adjoint_ws(int n, int batch);
 template <typename R>
 void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB<const typename cplx_of<R>::type> G,

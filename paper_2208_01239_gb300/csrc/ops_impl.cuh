@@ -391,6 +391,127 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   trsm<C, OP_C, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), X, nullptr, st);    // X2 = L^{-H} X1
 }
 
+// ------------------------------------------------------------------ linear solve
+// Algorithm "Linear system with Frobenius inversion" (Sec. 3) for nrhs
+// right-hand sides C + iD:  A = P1^T L1 U1; X1 = A^{-1} B; S = A + B X1;
+// S = P2^T L2 U2; [x1, y1] = S^{-1} [C, D]; [x2, y2] = A^{-1} B [y1, x1];
+// x = x1 + x2, y = y1 - y2 (the printed last step has y2 - y1; eq. (1.1)
+// gives y1 - y2).
+template <typename R>
+__global__ void rhs_split_kernel(int n, int nrhs, MatB<const typename cplx_of<R>::type> Bc, MatB<R> CD) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * nrhs) return;
+  const int i = (int)(e / nrhs), j = (int)(e % nrhs);
+  const auto v = Bc.at(b)[(int64_t)i * Bc.ld + j];
+  CD.at(b)[(int64_t)i * CD.ld + j] = v.x;
+  CD.at(b)[(int64_t)i * CD.ld + nrhs + j] = v.y;
+}
+
+template <typename R>
+__global__ void solve_out_kernel(int n, int nrhs, MatB<const R> T, MatB<const R> U,
+                                 MatB<typename cplx_of<R>::type> X) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * nrhs) return;
+  const int i = (int)(e / nrhs), j = (int)(e % nrhs);
+  const R* t = T.at(b) + (int64_t)i * T.ld;
+  const R* u = U.at(b) + (int64_t)i * U.ld;
+  typename cplx_of<R>::type v;
+  v.x = t[j] + u[j];               // x = x1 + x2
+  v.y = t[nrhs + j] - u[nrhs + j];  // y = y1 - y2
+  X.at(b)[(int64_t)i * X.ld + j] = v;
+}
+
+inline dim3 rect_grid(int n, int m, int batch) {
+  int64_t nn = (int64_t)n * m;
+  return dim3((unsigned)((nn + 255) / 256), 1, (unsigned)batch);
+}
+
+template <typename R> struct SolvePlanes {
+  MatB<R> LA, S, Bp, X1, CD, T, U;
+  int *piv1, *piv2, *rp1, *rp2;
+};
+
+template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlanes<R>* out, void* ws) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  SolvePlanes<R> p;
+  p.LA = plane<R>(c, n, batch);
+  p.S = plane<R>(c, n, batch);
+  p.Bp = plane<R>(c, n, batch);
+  p.X1 = plane<R>(c, n, batch);
+  auto rect = [&]() {
+    R* q = c.take<R>((size_t)n * 2 * nrhs * batch);
+    return MatB<R>{q, 2 * (int64_t)nrhs, (int64_t)n * 2 * nrhs};
+  };
+  p.CD = rect();
+  p.T = rect();
+  p.U = rect();
+  p.piv1 = c.take<int>((size_t)n * batch);
+  p.piv2 = c.take<int>((size_t)n * batch);
+  p.rp1 = c.take<int>((size_t)n * batch);
+  p.rp2 = c.take<int>((size_t)n * batch);
+  if (out) *out = p;
+  return c.off;
+}
+
+template <typename R>
+void frob_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::type> M,
+                    MatB<const typename cplx_of<R>::type> Bc, MatB<typename cplx_of<R>::type> X, void* ws,
+                    frob_info* info, cudaStream_t st) {
+  SolvePlanes<R> p;
+  frob_solve_ws<R>(n, nrhs, batch, &p, ws);
+  auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  const int m2 = 2 * nrhs;
+  FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, 0, 0, 0));
+  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                              // step 1
+  rowperm(n, batch, p.piv1, p.rp1, st);
+  trsm<R, OP_N, true, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);          // step 2
+  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st);
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.X1), axpby<R>(p.S, (R)1, (R)1, false), 0, st);  // 3
+  getrf<R>(n, batch, p.S, p.piv2, info, n, st);                                               // step 4
+  rowperm(n, batch, p.piv2, p.rp2, st);
+  FROB_LAUNCH("rhs_split", st, rhs_split_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, Bc, p.CD));
+  trsm<R, OP_N, true, true, false>(n, m2, batch, cst(p.S), cst(p.CD), p.T, p.rp2, st);          // step 5
+  trsm<R, OP_N, false, false, false>(n, m2, batch, cst(p.S), cst(p.T), p.T, nullptr, st);     // T = [x1 | y1]
+  // step 6: CD = B [y1 | x1], then U = A^{-1} CD = [x2 | y2]
+  MatB<const R> Ty{p.T.p + nrhs, p.T.ld, p.T.bs}, Tx{p.T.p, p.T.ld, p.T.bs};
+  gemm_launch<R, OP_N, OP_N>(n, nrhs, n, batch, cst(p.Bp), Ty, axpby<R>(p.CD, (R)1, (R)0, true), 0, st);
+  gemm_launch<R, OP_N, OP_N>(n, nrhs, n, batch, cst(p.Bp), Tx,
+                             axpby<R>(MatB<R>{p.CD.p + nrhs, p.CD.ld, p.CD.bs}, (R)1, (R)0, true), 0, st);
+  trsm<R, OP_N, true, true, false>(n, m2, batch, cst(p.LA), cst(p.CD), p.U, p.rp1, st);
+  trsm<R, OP_N, false, false, false>(n, m2, batch, cst(p.LA), cst(p.U), p.U, nullptr, st);
+  FROB_LAUNCH("solve_out", st,
+              solve_out_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, cst(p.T), cst(p.U), X));  // 7
+}
+
+// Complex LU solve (the baseline): M = P^T L U, L Y = P C, U X = Y.
+template <typename C> size_t cplx_solve_ws(int n, int nrhs, int batch) {
+  Carve c{nullptr};
+  plane<C>(c, n, batch);
+  c.take<C>((size_t)n * nrhs * batch);
+  c.take<int>((size_t)n * batch);
+  c.take<int>((size_t)n * batch);
+  return c.off;
+}
+
+template <typename C>
+void cplx_solve_run(int n, int nrhs, int batch, MatB<const C> M, MatB<const C> Bc, MatB<C> X, void* ws,
+                    frob_info* info, cudaStream_t st) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  MatB<C> W = plane<C>(c, n, batch);
+  C* yp = c.take<C>((size_t)n * nrhs * batch);
+  int* piv = c.take<int>((size_t)n * batch);
+  int* rp = c.take<int>((size_t)n * batch);
+  MatB<C> Y{yp, nrhs, (int64_t)n * nrhs};
+  auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, W, info));
+  getrf<C>(n, batch, W, piv, info, 0, st);
+  rowperm(n, batch, piv, rp, st);
+  trsm<C, OP_N, true, true, false>(n, nrhs, batch, cst(W), Bc, Y, rp, st);
+  trsm<C, OP_N, false, false, false>(n, nrhs, batch, cst(W), cst(Y), X, nullptr, st);
+}
+
 // ------------------------------------------------------------------ adjoint
 // grad M = -X^H G X^H for X = M^{-1} (d(M^{-1}) = -M^{-1} dM M^{-1}), as two
 // complex products, each by Gauss's three real multiplications (Sec. 2,

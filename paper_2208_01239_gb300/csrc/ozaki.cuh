@@ -153,7 +153,8 @@ struct OzArgs {
   int n;          // square matrices: rows = cols = K = n
   int Kp;         // K padded to KB
   int batch;
-  int S;          // digits per operand
+  int S;          // digits per operand in the digit arrays (their layout)
+  int Su;         // leading digits used (<= S): pairs s, t <= Su with s + t <= Su + 1
   const int* expA;  // [2][batch][n]
   const int* expB;  // [2][batch][n]
   // RESID: RT planes (re, im): R^T, plus per-matrix sum of squares
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = args.n, S = args.S, batch = args.batch;
+  const int Su = args.Su;
   const int b = blockIdx.z >> 1;
   const int part = blockIdx.z & 1;  // 0: real part of the product, 1: imaginary part
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
         const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
-        for (int s = 1; s <= S && ok; ++s) {
+        for (int s = 1; s <= Su && ok; ++s) {
           const int za = (ap * S + (s - 1)) * batch + b;
           for (int ch = 0; ch < nch && ok; ++ch) {
             const int kb0 = ch * A_CHUNK_KB;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int kb = kb0; kb < kb1; ++kb)
               tma_load_3d(abuf + (kb - kb0) * (BM * KB * 2), &mapA, &a_full[slot], kb * KB, m0, za);
             ++ai;
-            for (int t = 1; t <= S + 1 - s && ok; ++t) {
+            for (int t = 1; t <= Su + 1 - s && ok; ++t) {
               const int zb = (bp * S + (t - 1)) * batch + b;
               for (int kb = kb0; kb < kb1; ++kb) {
                 const int st = bi % B_STAGES;
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (term == 1 && !mbar_wait(drained, 0)) { ok = false; break; }  // groups drained after term 0
         tc_fence_after();
         uint32_t started = 0;
-        for (int s = 1; s <= S && ok; ++s) {
+        for (int s = 1; s <= Su && ok; ++s) {
           for (int ch = 0; ch < nch && ok; ++ch) {
             const int kb0 = ch * A_CHUNK_KB;
             const int kb1 = (kb0 + A_CHUNK_KB < nkb) ? kb0 + A_CHUNK_KB : nkb;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             ++ai;
             tc_fence_after();
             const uint32_t sa = smem_u32(a_res + slot * A_CHUNK_BYTES);
-            for (int t = 1; t <= S + 1 - s && ok; ++t) {
+            for (int t = 1; t <= Su + 1 - s && ok; ++t) {
               const int g = group_of(s, t);
               const uint32_t dt = tmem + (uint32_t)(g * BN);
               for (int kb = kb0; kb < kb1; ++kb) {
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         __syncwarp();
         const int ea = row < n ? args.expA[((int64_t)ap * batch + b) * n + row] : 0;
-        const int ngroups = (S <= 6) ? S : NUM_GROUPS;  // weights 2 .. S+1 -> groups 0 .. S-1 for S <= 6
+        const int ngroups = (Su <= 6) ? Su : NUM_GROUPS;  // weights 2 .. Su+1 -> groups 0 .. Su-1 for Su <= 6
         for (int g = 0; g < ngroups; ++g) {
           const int w = weight_of_group(g);
           // sign x 2^(e_A - 7 w): exact power of two (within FP32 range for the data seen here)

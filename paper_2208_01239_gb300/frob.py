@@ -103,6 +103,12 @@ def load() -> ctypes.CDLL:
         lib.frob_inv_batched_workspace_bytes.restype = sz
         lib.frob_inv_batched.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
         lib.frob_inv_batched.restype = i32
+        lib.frob_solve_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
+        lib.frob_solve_workspace_bytes.restype = sz
+        for name in ("frob_solve", "cplx_lu_solve"):
+            f = getattr(lib, name)
+            f.argtypes = [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, i32, vp, sz, vp, vp]
+            f.restype = i32
         lib.frob_gemm_tc.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, sz, vp,
                                      vp]
         lib.frob_gemm_tc.restype = i32
@@ -308,6 +314,54 @@ def frob_inv_batched(mats, op: str = "frob_inv", prec: str = "fp64", check: bool
     if check:
         check_info(info, "frob_inv_batched")
     return plan.outputs, info
+
+
+def _solve(name: str, op: int, m: torch.Tensor, rhs: torch.Tensor, prec: str, check: bool) -> Result:
+    lib = load()
+    on_host = not m.is_cuda
+    if on_host:
+        m, rhs = m.cuda(), rhs.cuda()
+    if m.dtype != _cdtype(prec) or rhs.dtype != m.dtype:
+        raise TypeError(f"{name}: expected {_cdtype(prec)} for prec={prec}")
+    m3 = m if m.dim() == 3 else m.unsqueeze(0)
+    r = rhs
+    if r.dim() == m.dim() - 1:
+        r = r.unsqueeze(-1)
+    r3 = r if r.dim() == 3 else r.unsqueeze(0)
+    m3, r3 = m3.contiguous(), r3.contiguous()
+    batch, n, nrhs = m3.shape[0], m3.shape[-1], r3.shape[-1]
+    x3 = torch.empty_like(r3)
+    need = int(lib.frob_solve_workspace_bytes(op, n, nrhs, batch, PREC[prec]))
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=m3.device)
+    pad = (-ws.data_ptr()) % 256
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=m3.device)
+    st = getattr(lib, name)(n, nrhs, batch, m3.data_ptr(), m3.stride(1), m3.stride(0), r3.data_ptr(), r3.stride(1),
+                            r3.stride(0), x3.data_ptr(), x3.stride(1), x3.stride(0), PREC[prec], ws.data_ptr() + pad,
+                            ws.numel() - pad, info.data_ptr(), torch.cuda.current_stream(m3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"{name}: {status_str(st)}", st)
+    x = x3
+    if r.dim() != rhs.dim():
+        x = x.squeeze(-1)
+    if m.dim() == 2:
+        x = x[0]
+    res = Result(x, info)
+    if check:
+        check_info(res.info(), name)
+    if on_host:
+        res.x = res.x.cpu()
+    return res
+
+
+def frob_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bool = True) -> Result:
+    """Solve M X = RHS by Frobenius inversion without forming M^{-1} (Sec. 3);
+    m: (n, n) or (batch, n, n); rhs: (..., n) or (..., n, nrhs)."""
+    return _solve("frob_solve", 0, m, rhs, prec, check)
+
+
+def cplx_lu_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bool = True) -> Result:
+    """Solve M X = RHS by complex LU with partial pivoting (baseline)."""
+    return _solve("cplx_lu_solve", 1, m, rhs, prec, check)
 
 
 def inv_adjoint(x: torch.Tensor, g: torch.Tensor, prec: str | None = None) -> torch.Tensor:

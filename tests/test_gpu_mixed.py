@@ -44,10 +44,12 @@ def test_mixed_vs_oracle(F, prec, n):
         # bounded by kappa times the attained residual (plus FP64 rounding)
         kappa = np.linalg.cond(ms[b])
         assert metrics.forward_error(x[b], ref) <= 32 * n * kappa * U64 + 4 * np.sqrt(n) * kappa * res
-        # the device-side residual (49-bit digit products, resolution ~2^-48
-        # relative to |M||X|) agrees with the host's FP64 evaluation (itself
-        # noisy at ~sqrt(n) u at this level)
-        tol = 0.05 * res + 2.0 ** -48 + 4 * np.sqrt(n) * U64
+        # the device-side residual agrees with the host's FP64 evaluation to
+        # the resolution of both: 7-digit products are within ~2^-46 of the
+        # exact product relative to |M||X| (each operand truncated at 2^-50 of
+        # a scale up to twice its row maximum, plus the dropped digit pairs),
+        # and the host's own evaluation is noisy at ~sqrt(n) u
+        tol = 0.05 * res + 2.0 ** -46 + 4 * np.sqrt(n) * U64
         assert abs(info["residual"][b] - res) <= tol, (info["residual"][b], res)
         assert info["ns_iters"][b] >= 1 or n == 1
 
