@@ -196,6 +196,56 @@ def measure_batched(frob, dev, steps, rank):
     return out
 
 
+def measure_solve(frob, dev, steps):
+    """Linear systems (Sec. 5.2): 16 systems of order 512, one right-hand
+    side, A and B from the kappa = 10 generator of Sec. 5.1 and x, y uniform
+    on [-1, 1] with c + id = M (x + iy); and the ill-conditioned construction
+    of Sec. 3 (kappa(M) ~ 2e6, kappa(A) = kappa(B) = 1).  Frobenius solve vs
+    complex-LU solve: relative forward error (max norm) and solves/s."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+    n, batch = 512, 16
+    g = np.random.default_rng(12)
+    out = {}
+    cases = {}
+    ms = np.stack([W.kappa_controlled(n, 10.0, seed=100 + k) for k in range(batch)])
+    xs = g.uniform(-1, 1, (batch, n, 1)) + 1j * g.uniform(-1, 1, (batch, n, 1))
+    cases["kappa10"] = (ms, ms @ xs, xs)
+    mi = []
+    xi = []
+    for k in range(batch):
+        m, minv = W.ill_conditioned(n, seed=200 + k)
+        b = g.standard_normal((n, 1)) + 1j * g.standard_normal((n, 1))
+        mi.append(m)
+        xi.append((minv @ b, b))
+    cases["ill_conditioned"] = (np.stack(mi), np.stack([b for _, b in xi]), np.stack([x for x, _ in xi]))
+    for cname, (m, rhs, xtrue) in cases.items():
+        dm = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+        dr = torch.from_numpy(np.ascontiguousarray(rhs)).to(dev)
+        res = {}
+        for method in ("frob_solve", "cplx_lu_solve"):
+            f = getattr(frob, method)
+            x = f(dm, dr, check=False).x
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                x = f(dm, dr, check=False).x
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms_ = e0.elapsed_time(e1) / steps
+            xn = x.cpu().numpy()
+            fe = max(float(np.max(np.abs(np.concatenate([(xn[k] - xtrue[k]).real.ravel(), (xn[k] - xtrue[k]).imag.ravel()])))) /
+                     float(max(np.abs(xtrue[k].real).max(), np.abs(xtrue[k].imag).max())) for k in range(batch))
+            res[method] = {"forward_error_max": fe, "solves_per_s": batch / (ms_ * 1e-3), "ms_per_step": ms_}
+        out[cname] = res
+    out["n"] = n
+    out["batch"] = batch
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,6 +400,7 @@ def main():
                            sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]}}
 
     batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
+    solve = None if args.no_batched else measure_solve(frob, dev, 3)
 
     # end to end through the public API with host buffers
     def e2e_step():
@@ -396,6 +447,7 @@ def main():
                         "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)} for k, v in prof.items()},
         "mixed": mixed,
         "batched_uneven": batched,
+        "linear_solve": solve,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),
