@@ -353,8 +353,8 @@ constexpr int PANEL_THREADS = 512;
 
 // LU with partial pivoting of the column panel [k0, k0+kb) over rows [k0, n)
 // of each matrix (grid: batch).  The panel is staged in shared memory when
-// `staged` (rows * kb * sizeof(T) fits), else factored in place in global
-// memory.  piv[k] (absolute row, batch stride n) receives the row exchanged
+// `staged` (rows * (kb + 1) * sizeof(T) fits), else factored in place in
+// global memory.  piv[k] (absolute row, batch stride n) receives the row exchanged
 // with row k.  A zero or non-finite pivot reports FROB_ERR_SINGULAR with
 // bad_index = k + 1 + info_off and leaves that column unscaled.
 template <typename T>
@@ -373,9 +373,10 @@ __global__ void __launch_bounds__(PANEL_THREADS) getrf_panel_kernel(int n, int k
   T* P;
   int64_t ps;
   if (staged) {
+    // row stride kb + 1: a warp reading one column touches 32 different banks
     P = reinterpret_cast<T*>(smraw);
-    ps = kb;
-    for (int e = t; e < m * kb; e += PANEL_THREADS) P[e] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
+    ps = kb + 1;
+    for (int e = t; e < m * kb; e += PANEL_THREADS) P[(e / kb) * ps + (e % kb)] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
     __syncthreads();
   } else {
     P = g;
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) getrf_panel_kernel(int n, int k
     __syncthreads();
   }
   if (staged) {
-    for (int e = t; e < m * kb; e += PANEL_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[e];
+    for (int e = t; e < m * kb; e += PANEL_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[(e / kb) * ps + (e % kb)];
   }
 }
 

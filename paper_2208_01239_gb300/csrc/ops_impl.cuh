@@ -200,7 +200,7 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
-    const size_t bytes = (size_t)(n - k0) * kb * sizeof(T);
+    const size_t bytes = (size_t)(n - k0) * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
     FROB_LAUNCH(getrf_panel_name<T>(), st, getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info, info_off,
                                                                             staged));
