@@ -4,8 +4,8 @@
 //   repeat:  R = I - M X        FP64-accurate (digit-split products on the
 //                               BF16 tensor cores, ozaki.cuh)
 //            stop when ||R||_F / (||M||_F ||X||_F) <= tol
-//            X <- X + X R       (4 digits per operand: ~2^-28 relative, ample
-//                               for a correction that is itself ~||R|| X)
+//            X <- X + X R       (4 digits per operand in the first
+//                               correction, 5 after it: see S_CORR)
 //
 // X is kept in FP64 (planes X and X^T, so that both products only ever split
 // rows).  Matrices that have converged, or whose FP32 inversion failed, are
@@ -27,9 +27,26 @@
 namespace frob {
 namespace mixed {
 
+// Digits of M and X in the residual I - M X.  A computed residual R~_k =
+// R_k + E_k feeds the next one as R_{k+1} = R_k^2 - E_k + R_k E_k, so the
+// error of every residual but the first bounds what the refinement can reach.
+// Seven digits (pairs s + t <= 8) leave dropped terms of weight 2^-63 times
+// the row and column scales: a relative residual floor near 1e-16 for
+// matrices whose entries are alike in size, and up to about 1e-14 when a
+// large diagonal sets the row scale (Hermitian positive definite input with a
+// wide spectrum).  Eight digits (pairs s + t <= 9) lower that floor by 2^7 and
+// are used when the requested tolerance is below 1e-14.
 constexpr int S_RESID = 7;
+constexpr int S_RESID_FINE = 8;
 constexpr int S_RESID_FIRST = 5;  // the first residual's error adds to ||R_0||^2: 2^-36 suffices
-constexpr int S_CORR = 4;
+// The correction X R is computed from S_CORR-digit splits of X and R (pairs
+// s + t <= S_CORR + 1), a relative error near 2^(-7 S_CORR - 1) of X R, so the
+// next residual is R^2 + O(2^(-7 S_CORR - 1) ||R||).  Four digits suffice for
+// the first correction (||R_0|| ~ FP32 accuracy, R_0^2 dominates); later
+// ones use five, or the 2^-29 ||R_1|| term would stall the relative residual
+// near 1e-14.
+constexpr int S_CORR = 5;
+constexpr int S_CORR_FIRST = 4;
 
 namespace {
 
@@ -182,14 +199,21 @@ void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs
               oz::oz_cgemm_kernel<MODE><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ma, mb, a));
 }
 
+// joint: the real and imaginary rows share one exponent (operands of the
+// residual product)
 void launch_split(int n, int Kp, int batch, int S, const double* src, __nv_bfloat16* dst, int* exps,
-                  const int* skip, cudaStream_t st) {
-  const int64_t warps = (int64_t)2 * batch * n;
+                  const int* skip, bool joint, cudaStream_t st) {
+  const int64_t warps = (int64_t)(joint ? 1 : 2) * batch * n;
   const int threads = 256;
   const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
-  FROB_LAUNCH("oz_split", st,
-              oz::oz_split_rows_kernel<<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
-                                                                   (int64_t)batch * n * n, dst, exps, skip));
+  if (joint)
+    FROB_LAUNCH("oz_split", st,
+                oz::oz_split_rows_kernel<true><<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
+                                                                           (int64_t)batch * n * n, dst, exps, skip));
+  else
+    FROB_LAUNCH("oz_split", st,
+                oz::oz_split_rows_kernel<false><<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
+                                                                            (int64_t)batch * n * n, dst, exps, skip));
 }
 
 struct Layout {
@@ -213,7 +237,7 @@ Layout carve(int n, int batch, void* ws) {
     return p;
   };
   const size_t nn = (size_t)n * n;
-  const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
+  const int Kp = (n + oz::KP_ALIGN - 1) / oz::KP_ALIGN * oz::KP_ALIGN;
   L.M32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
   L.X32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
   const size_t w_lu = frob_lu_ws<float>(n, batch, nullptr, nullptr);
@@ -247,7 +271,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
                       cudaStream_t st, bool hpd) {
   if (n > oz::K_MAX) return FROB_ERR_UNSUPPORTED;
   Layout L = carve(n, batch, ws);
-  const int Kp = (n + oz::KB - 1) / oz::KB * oz::KB;
+  const int Kp = (n + oz::KP_ALIGN - 1) / oz::KP_ALIGN * oz::KP_ALIGN;
   const int64_t nn = (int64_t)n * n;
   const dim3 eg((unsigned)((nn + 255) / 256), 1, batch);
   const double tol = o.ns_tol > 0 ? o.ns_tol : 1e-14;
@@ -267,21 +291,22 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
     frob_lu_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, o32, L.ws32, info, st);
   FROB_LAUNCH("mixed_conv_x", st, conv_x_kernel<<<eg, 256, 0, st>>>(n, MatB<const zf>{L.X32, n, nn}, L.Xp, L.XTp, batch));
   FROB_LAUNCH("mixed_init_skip", st, init_skip_kernel<<<(batch + 127) / 128, 128, 0, st>>>(info, L.skip, batch));
-  launch_split(n, Kp, batch, S_RESID, L.Mp, L.Mdig, L.expM, L.skip, st);
+  const int s_resid = tol < 1e-14 ? S_RESID_FINE : S_RESID;
+  launch_split(n, Kp, batch, s_resid, L.Mp, L.Mdig, L.expM, L.skip, true, st);
 
-  CUtensorMap mapM, mapXT7, mapX3, mapRT3;
-  if (!digit_map(&mapM, L.Mdig, n, Kp, S_RESID, batch, tc::BM) ||
-      !digit_map(&mapXT7, L.Bdig, n, Kp, S_RESID, batch, oz::BN) ||
-      !digit_map(&mapX3, L.Xdig, n, Kp, S_CORR, batch, tc::BM) ||
-      !digit_map(&mapRT3, L.Bdig, n, Kp, S_CORR, batch, oz::BN))
+  CUtensorMap mapM, mapXTr, mapXc, mapRTc;
+  if (!digit_map(&mapM, L.Mdig, n, Kp, s_resid, batch, tc::BM) ||
+      !digit_map(&mapXTr, L.Bdig, n, Kp, s_resid, batch, oz::BN) ||
+      !digit_map(&mapXc, L.Xdig, n, Kp, S_CORR, batch, tc::BM) ||
+      !digit_map(&mapRTc, L.Bdig, n, Kp, S_CORR, batch, oz::BN))
     return FROB_ERR_CUDA;
 
   oz::OzArgs ra{};
   ra.n = n;
   ra.Kp = Kp;
   ra.batch = batch;
-  ra.S = S_RESID;
-  ra.Su = S_RESID;
+  ra.S = s_resid;
+  ra.Su = s_resid;
   ra.expA = L.expM;
   ra.expB = L.expB;
   ra.outR = L.RTp;
@@ -299,16 +324,17 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
     FROB_LAUNCH("mixed_zero", st, zero_kernel<<<(batch + 127) / 128, 128, 0, st>>>(L.rn2, L.nX2, batch, L.skip));
     const dim3 xg((unsigned)((nn + 256 * XN_PER_THREAD - 1) / (256 * XN_PER_THREAD)), 1, batch);
     FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<xg, 256, 0, st>>>(n, L.Xp, L.nX2, batch, L.skip));
-    launch_split(n, Kp, batch, S_RESID, L.XTp, L.Bdig, L.expB, L.skip, st);
-    ra.Su = it == 0 ? S_RESID_FIRST : S_RESID;
-    launch_cgemm<oz::RESID>(mapM, mapXT7, ra, st);                                   // R = I - M X
+    launch_split(n, Kp, batch, s_resid, L.XTp, L.Bdig, L.expB, L.skip, true, st);
+    ra.Su = it == 0 ? S_RESID_FIRST : s_resid;
+    launch_cgemm<oz::RESID>(mapM, mapXTr, ra, st);                                   // R = I - M X
     FROB_LAUNCH("mixed_check", st,
                 check_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, it, it == max_iter, tol, L.rn2, L.nM2, L.nX2,
                                                                   L.skip, info));
     if (it == max_iter) break;
-    launch_split(n, Kp, batch, S_CORR, L.Xp, L.Xdig, L.expX, L.skip, st);
-    launch_split(n, Kp, batch, S_CORR, L.RTp, L.Bdig, L.expB, L.skip, st);
-    launch_cgemm<oz::CORR>(mapX3, mapRT3, ca, st);                                   // X <- X + X R
+    launch_split(n, Kp, batch, S_CORR, L.Xp, L.Xdig, L.expX, L.skip, false, st);
+    launch_split(n, Kp, batch, S_CORR, L.RTp, L.Bdig, L.expB, L.skip, false, st);
+    ca.Su = it == 0 ? S_CORR_FIRST : S_CORR;
+    launch_cgemm<oz::CORR>(mapXc, mapRTc, ca, st);                                   // X <- X + X R
   }
   FROB_LAUNCH("mixed_conv_out", st, conv_out_kernel<<<eg, 256, 0, st>>>(n, L.Xp, X, batch));
   return cudaGetLastError() == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;

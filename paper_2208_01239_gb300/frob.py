@@ -221,27 +221,33 @@ def _call(op: str, m: torch.Tensor, prec: str, opts: FrobOpts | None, out: torch
     return res
 
 
-def _opts(prec: str, almost_sure: bool = False, seed: int = 0, attempt: int = 0) -> FrobOpts:
+def _opts(prec: str, almost_sure: bool = False, seed: int = 0, attempt: int = 0, ns_tol: float = 1e-14,
+          ns_max_iter: int = 8) -> FrobOpts:
     o = FrobOpts()
     o.prec = PREC[prec]
     o.almost_sure = 1 if almost_sure else 0
     o.seed = seed
     o.attempt = attempt
-    o.ns_max_iter = 8
-    o.ns_tol = 1e-14
+    o.ns_max_iter = ns_max_iter
+    o.ns_tol = ns_tol
     return o
 
 
 def frob_inv(m: torch.Tensor, prec: str = "fp64", almost_sure: bool = False, seed: int = 0, attempt: int = 0,
-             out=None, ws=None, info=None, check: bool = True) -> Result:
-    """(A + iB)^{-1} = S^{-1} - i A^{-1} B S^{-1}, S = A + B A^{-1} B."""
-    return _call("frob_inv", m, prec, _opts(prec, almost_sure, seed, attempt), out, ws, info, check)
+             out=None, ws=None, info=None, check: bool = True, ns_tol: float = 1e-14, ns_max_iter: int = 8) -> Result:
+    """(A + iB)^{-1} = S^{-1} - i A^{-1} B S^{-1}, S = A + B A^{-1} B.
+
+    ns_tol / ns_max_iter: stopping rule of the mixed precisions' Newton-Schulz
+    refinement (relative residual ||I - M X||_F / (||M||_F ||X||_F))."""
+    return _call("frob_inv", m, prec, _opts(prec, almost_sure, seed, attempt, ns_tol, ns_max_iter), out, ws, info,
+                 check)
 
 
-def frob_inv_hpd(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
+def frob_inv_hpd(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True,
+                 ns_tol: float = 1e-14, ns_max_iter: int = 8) -> Result:
     """Frobenius inversion with two real Cholesky factorisations (HPD input,
     lower triangle read)."""
-    return _call("frob_inv_hpd", m, prec, _opts(prec), out, ws, info, check)
+    return _call("frob_inv_hpd", m, prec, _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter), out, ws, info, check)
 
 
 def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
