@@ -370,34 +370,39 @@ def main():
 
     # the mixed form on the same workload: FP32 Cholesky-Frobenius start,
     # Newton-Schulz refinement with FP64-accurate products on the BF16 tensor
-    # cores, same residual gate
+    # cores, same residual gate; at the default tolerance (7-digit residuals)
+    # and at 1e-15 (8-digit residuals, a residual floor near the FP64 paths')
     need_m = frob.workspace_bytes("frob_inv_hpd", N_ORDER, BATCH, "mixed_bf16")
     ws_m = torch.empty(need_m + 256, dtype=torch.uint8, device=dev)
 
-    def step_mixed():
-        frob.frob_inv_hpd(m_dev, prec="mixed_bf16", out=x_dev, ws=ws_m, info=info, check=False)
+    def measure_mixed(tol):
+        def step_mixed():
+            frob.frob_inv_hpd(m_dev, prec="mixed_bf16", out=x_dev, ws=ws_m, info=info, check=False, ns_tol=tol)
 
-    for _ in range(args.warmup):
-        step_mixed()
-    torch.cuda.synchronize(dev)
-    frob.profile_enable(True)
-    tm_ms = timed(step_mixed, args.steps) / args.steps
-    frob.profile_enable(False)
-    prof_m = frob.profile_report()
-    inf_m = frob.parse_info(info)
-    xm = x_dev.cpu().numpy()
-    res_m = max(residual_fro(ms[b], xm[b]) for b in (0, BATCH // 2, BATCH - 1))
-    tot_m = max(sum(v[1] for v in prof_m.values()), 1e-30)
-    mixed = {"name": "frob_inv_hpd prec=mixed_bf16", "value": world * BATCH / (tm_ms * 1e-3), "unit": "inversions/s",
-             "ms_per_step": tm_ms, "residual_fro_max_sampled": res_m,
-             "residual_fro_max_device": float(inf_m["residual"].max()),
-             "status_ok": int((inf_m["status"] == 0).sum()),
-             "ns_iters_hist": np.bincount(inf_m["ns_iters"], minlength=1).tolist(),
-             "dtype": "bf16 tensor cores + fp32 (results FP64-accurate)",
-             "top_kernels": {k: round(v[1] / args.steps, 3) for k, v in
-                             sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]},
-             "top_share": {k: round(v[1] / tot_m, 3) for k, v in
-                           sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]}}
+        for _ in range(args.warmup):
+            step_mixed()
+        torch.cuda.synchronize(dev)
+        frob.profile_enable(True)
+        tm_ms = timed(step_mixed, args.steps) / args.steps
+        frob.profile_enable(False)
+        prof_m = frob.profile_report()
+        inf_m = frob.parse_info(info)
+        xm = x_dev.cpu().numpy()
+        res_m = max(residual_fro(ms[b], xm[b]) for b in (0, BATCH // 2, BATCH - 1))
+        tot_m = max(sum(v[1] for v in prof_m.values()), 1e-30)
+        return {"name": "frob_inv_hpd prec=mixed_bf16", "ns_tol": tol, "value": world * BATCH / (tm_ms * 1e-3),
+                "unit": "inversions/s", "ms_per_step": tm_ms, "residual_fro_max_sampled": res_m,
+                "residual_fro_max_device": float(inf_m["residual"].max()),
+                "status_ok": int((inf_m["status"] == 0).sum()),
+                "ns_iters_hist": np.bincount(inf_m["ns_iters"], minlength=1).tolist(),
+                "dtype": "bf16 tensor cores + fp32 (results FP64-accurate)",
+                "top_kernels": {k: round(v[1] / args.steps, 3) for k, v in
+                                sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]},
+                "top_share": {k: round(v[1] / tot_m, 3) for k, v in
+                              sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]}}
+
+    mixed = measure_mixed(1e-14)
+    mixed_fine = measure_mixed(1e-15)
 
     batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
     solve = None if args.no_batched else measure_solve(frob, dev, 3)
@@ -446,6 +451,7 @@ def main():
         "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                         "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)} for k, v in prof.items()},
         "mixed": mixed,
+        "mixed_tol_1e-15": mixed_fine,
         "batched_uneven": batched,
         "linear_solve": solve,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,

@@ -199,21 +199,14 @@ void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs
               oz::oz_cgemm_kernel<MODE><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ma, mb, a));
 }
 
-// joint: the real and imaginary rows share one exponent (operands of the
-// residual product)
 void launch_split(int n, int Kp, int batch, int S, const double* src, __nv_bfloat16* dst, int* exps,
-                  const int* skip, bool joint, cudaStream_t st) {
-  const int64_t warps = (int64_t)(joint ? 1 : 2) * batch * n;
+                  const int* skip, cudaStream_t st) {
+  const int64_t warps = (int64_t)batch * n;  // one warp per (real, imaginary) row pair
   const int threads = 256;
   const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
-  if (joint)
-    FROB_LAUNCH("oz_split", st,
-                oz::oz_split_rows_kernel<true><<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
-                                                                           (int64_t)batch * n * n, dst, exps, skip));
-  else
-    FROB_LAUNCH("oz_split", st,
-                oz::oz_split_rows_kernel<false><<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
-                                                                            (int64_t)batch * n * n, dst, exps, skip));
+  FROB_LAUNCH("oz_split", st,
+              oz::oz_split_rows_kernel<<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
+                                                                   (int64_t)batch * n * n, dst, exps, skip));
 }
 
 struct Layout {
@@ -292,7 +285,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   FROB_LAUNCH("mixed_conv_x", st, conv_x_kernel<<<eg, 256, 0, st>>>(n, MatB<const zf>{L.X32, n, nn}, L.Xp, L.XTp, batch));
   FROB_LAUNCH("mixed_init_skip", st, init_skip_kernel<<<(batch + 127) / 128, 128, 0, st>>>(info, L.skip, batch));
   const int s_resid = tol < 1e-14 ? S_RESID_FINE : S_RESID;
-  launch_split(n, Kp, batch, s_resid, L.Mp, L.Mdig, L.expM, L.skip, true, st);
+  launch_split(n, Kp, batch, s_resid, L.Mp, L.Mdig, L.expM, L.skip, st);
 
   CUtensorMap mapM, mapXTr, mapXc, mapRTc;
   if (!digit_map(&mapM, L.Mdig, n, Kp, s_resid, batch, tc::BM) ||
@@ -324,15 +317,15 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
     FROB_LAUNCH("mixed_zero", st, zero_kernel<<<(batch + 127) / 128, 128, 0, st>>>(L.rn2, L.nX2, batch, L.skip));
     const dim3 xg((unsigned)((nn + 256 * XN_PER_THREAD - 1) / (256 * XN_PER_THREAD)), 1, batch);
     FROB_LAUNCH("mixed_xnorm", st, xnorm_kernel<<<xg, 256, 0, st>>>(n, L.Xp, L.nX2, batch, L.skip));
-    launch_split(n, Kp, batch, s_resid, L.XTp, L.Bdig, L.expB, L.skip, true, st);
+    launch_split(n, Kp, batch, s_resid, L.XTp, L.Bdig, L.expB, L.skip, st);
     ra.Su = it == 0 ? S_RESID_FIRST : s_resid;
     launch_cgemm<oz::RESID>(mapM, mapXTr, ra, st);                                   // R = I - M X
     FROB_LAUNCH("mixed_check", st,
                 check_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, it, it == max_iter, tol, L.rn2, L.nM2, L.nX2,
                                                                   L.skip, info));
     if (it == max_iter) break;
-    launch_split(n, Kp, batch, S_CORR, L.Xp, L.Xdig, L.expX, L.skip, false, st);
-    launch_split(n, Kp, batch, S_CORR, L.RTp, L.Bdig, L.expB, L.skip, false, st);
+    launch_split(n, Kp, batch, S_CORR, L.Xp, L.Xdig, L.expX, L.skip, st);
+    launch_split(n, Kp, batch, S_CORR, L.RTp, L.Bdig, L.expB, L.skip, st);
     ca.Su = it == 0 ? S_CORR_FIRST : S_CORR;
     launch_cgemm<oz::CORR>(mapXc, mapRTc, ca, st);                                   // X <- X + X R
   }

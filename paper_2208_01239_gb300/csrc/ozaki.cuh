@@ -3,46 +3,49 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 2012, scheme I).
 //
-// Splitting (oz_split_rows_kernel).  Each row i of a real FP64 matrix is
-// scaled by 2^-e_i, where 2^e_i is the smallest power of two above the row's
-// largest magnitude, so the scaled entries r lie in (-1, 1).  Then S signed
-// digits are taken by repeated round-to-nearest:
-//     d_1 = rint(128 r),  r <- 128 r - d_1,  d_2 = rint(128 r), ...
-// |d_1| <= 128 and |d_s| <= 64 for s >= 2, so every digit is exact in BF16,
-// and  r = sum_s d_s 2^{-7 s} + (remainder below 2^{-7 S - 1}).
+// Splitting (oz_split_rows_kernel).  Each row i of a real FP64 matrix pair
+// (the real and imaginary parts) is scaled by 2^-e_i, where 2^e_i is the
+// smallest power of two above the largest magnitude in the two rows, so the
+// scaled entries r lie in (-1, 1).  Then r is written with S signed digits
+// in base 128, r = sum_s d_s 2^{-7 s} + (remainder below 2^{-7 S - 1}),
+// |d_1| <= 128 and |d_s| <= 64 for s >= 2, so every digit is exact in BF16.
 //
 // Products.  For digit matrices D_s (of A, row-scaled) and E_t (of B,
 // column-scaled), every entry of D_s E_t^T is an integer below 2^23 in
 // magnitude when K <= 512, so the tensor core's FP32 accumulation is exact.
 // All pairs with the same weight 2^{-7 (s + t)} are accumulated into one TMEM
-// accumulator; for s + t <= 7 the sum stays at most 2^24 and is exact.  The
-// weights 2^-56 and 2^-63 (s + t = 8, 9) lie below the FP64 unit of the
-// result, so one FP32 rounding of their group sums (relative 2^-24) is
+// accumulator ("group"); for s + t <= 7 the sum stays at most 2^24 and is
+// exact.  The weights 2^-56 and 2^-63 (s + t = 8, 9) lie below the FP64 unit
+// of the result, so one FP32 rounding of their group sums (relative 2^-24) is
 // harmless there.  Pairs with s + t > S + 1 are dropped (their weight is
 // below 2^{-7 (S + 2)}).
 //
 // Complex product C = A B with A = Ar + i Ai, B = Br + i Bi:
 //   Re C = Ar Br - Ai Bi,  Im C = Ar Bi + Ai Br;
-// each output part is two real terms.  The kernel computes one 128 x 64 tile
-// of one part: for each term, for each digit s of the A operand, for each
-// 256-wide K chunk, the 128 x 256 chunk of the digit slice stays resident in
-// shared memory (two chunk buffers, so that the next chunk loads while the
-// current one is used) while the matching K chunks of the digit slices of B
-// stream through a 6-stage TMA ring of 128-wide K stages (8 MMAs per barrier
-// round: the per-round barrier and commit cost is fixed, so wider stages keep
-// the tensor pipe busier); tcgen05.mma accumulates into the group
-// accumulators in TMEM; after each term the epilogue warps add the groups,
-// scaled by their powers of two, into a register accumulator per output
-// element (see the epilogues below).  The final value goes to FP64.
+// each output part is two real terms, and with the joint exponents both
+// terms carry the same row and column scales.
 //
-// Epilogues:
+// Kernel (oz_cgemm_kernel): one 128 x 128 tile of one part per CTA.  The
+// tensor pipe spends about the same time on a 128 x 64 x 16 MMA as on a
+// 128 x 128 x 16 one, so the tile is 128 wide; TMEM (512 columns) then holds
+// four 128-column accumulator slots, fewer than the up to 8 groups of a term.
+// The groups are therefore issued in two bands, weights 2..5 and 6..S+1, each
+// of at most four groups; within a band the pairs go digit s of A outermost,
+// so that a group's last pair (largest s) comes early for the heavy weights
+// and every group is complete, and drained by the epilogue warps, while the
+// tensor core works on later groups.  Group g of the tile (both terms, in
+// order) lives in slot g mod 4; an MMA into a slot waits until the epilogue
+// has drained the group that held it before.  Operands: for each digit s of A
+// and each 128-wide K chunk, the 128 x 128 chunk of the digit slice stays in
+// shared memory (double buffered) while the matching chunks of the B digit
+// slices t of the band stream through a 5-stage TMA ring (8 MMAs per stage).
+//
+// Epilogue (8 warps; warp w reads TMEM lanes 32 (w mod 4) .. + 31 and one
+// 64-column half): each group is added, exactly, into a 64-bit fixed-point
+// accumulator per element in units of 2^-52 of the scaled product
+// (|scaled product| < 2^11), and the sum is converted to FP64 once:
 //   RESID:  writes R^T with R = I - A B (transposed store, coalesced) and
-//           adds sum |R_ij|^2 into a per-matrix FP64 accumulator.  The
-//           operands are split with joint real / imaginary exponents and the
-//           groups are summed exactly in 64-bit fixed point, so that the
-//           residual carries FP64 rounding only (float-float would leave an
-//           error near 2^-48 of sum_k |a_ik b_kj|, which is the floor the
-//           refinement would stall at).
+//           adds sum |R_ij|^2 into a per-matrix FP64 accumulator.
 //   CORR:   X <- X + A B, written to X (row-major) and X^T.
 #pragma once
 
@@ -58,33 +61,32 @@ namespace frob {
 namespace oz {
 
 constexpr int S_MAX = 8;
-constexpr int BN = 64;        // output tile columns
+constexpr int BN = 128;       // output tile columns (rows: tc::BM = 128)
 constexpr int KB = 64;        // BF16 elements per k-block (one 128-byte row)
 constexpr int KP_ALIGN = 128; // the padded K (digit-array pitch) is a multiple of this
 constexpr int K_MAX = 512;    // largest inner dimension with exact FP32 accumulation
-constexpr int A_CHUNK_KB = 4;                              // k-blocks per resident A chunk
-constexpr int A_CHUNK_BYTES = tc::BM * KB * 2 * A_CHUNK_KB;  // 64 KB: 128 rows x 256 K
-constexpr int A_RES_BYTES = 2 * A_CHUNK_BYTES;               // double-buffered
-constexpr int KSTAGE = 2;                                   // 64-wide K boxes per B stage
-constexpr int B_BOX_BYTES = BN * KB * 2;                    // 8 KB
-constexpr int B_STAGE_BYTES = B_BOX_BYTES * KSTAGE;         // 16 KB: 8 MMAs per barrier round
-constexpr int B_STAGES = 6;
-constexpr int NUM_GROUPS = 8;
-constexpr int THREADS = 192;
-constexpr int SMEM_BYTES = A_RES_BYTES + B_STAGES * B_STAGE_BYTES + 1024 + 512 + 4 * BN * 4;
-
-// weight group of the digit pair (s, t), 1-based digits, s + t <= 9: one
-// group per weight 2^(-7 (s + t))
-__host__ __device__ constexpr int group_of(int s, int t) { return s + t - 2; }
-__host__ __device__ constexpr int weight_of_group(int g) { return g + 2; }
+constexpr int CHUNK_KB = 2;                                // k-blocks per K chunk (128 K)
+constexpr int A_BOX_BYTES = tc::BM * KB * 2;               // 16 KB
+constexpr int A_CHUNK_BYTES = A_BOX_BYTES * CHUNK_KB;      // 32 KB
+constexpr int A_RES_BYTES = 2 * A_CHUNK_BYTES;             // double-buffered
+constexpr int B_BOX_BYTES = BN * KB * 2;                   // 16 KB
+constexpr int B_STAGE_BYTES = B_BOX_BYTES * CHUNK_KB;      // 32 KB: 8 MMAs per stage
+constexpr int B_STAGES = 5;
+constexpr int SLOTS = 4;                                   // 128-column TMEM accumulators
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;               // producer, MMA, epilogue warps
+constexpr int NUM_BARS = 2 * B_STAGES + 4 + 2 * SLOTS + 1;
+constexpr int SMEM_BYTES = A_RES_BYTES + B_STAGES * B_STAGE_BYTES + 1024 + NUM_BARS * 8 + 16;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+static_assert(KP_ALIGN == KB * CHUNK_KB, "one B stage per (digit pair, K chunk)");
 
 // ---------------------------------------------------------------- split
 // src: two real FP64 matrices per batch entry (rows x K, row-major, ld, batch
 // stride bs, part stride ps); dst digits: BF16 [part][s][b][row][Kp]
 // (zero-padded to Kp, Kp a multiple of 128, K <= K_MAX); exps: int
-// [part][b][row].  With JOINT the real and imaginary rows share one exponent
-// (the larger), so that the two real products of one complex output part
-// carry the same row and column scales.
+// [part][b][row].  The real and imaginary rows share one exponent (the
+// larger), so that the two real products of one complex output part carry
+// the same row and column scales.
 //
 // Integer arithmetic only (the FP64 pipe is slow on this GPU): with
 // x = +-m 2^(ex - 1075) (m the 53-bit significand, ex the biased exponent),
@@ -125,23 +127,21 @@ __device__ __forceinline__ uint32_t bf16_bits_of_int(int d) {
   return (uint32_t)__float_as_uint(f) >> 16;
 }
 
-// One warp per row (JOINT: per row pair, real and imaginary).  Each lane keeps
-// its 16 entries of the row (4 consecutive columns in each 128-wide block) in
+// One warp per row pair (real and imaginary).  Each lane keeps its 16
+// entries of each row (4 consecutive columns in each 128-wide block) in
 // registers between the maximum and the digit passes.
-template <bool JOINT>
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Kp, int batch, int S,
                                                             const double* src, int64_t ld, int64_t bs, int64_t ps,
                                                             __nv_bfloat16* dst, int* exps, const int* skip) {
-  constexpr int NP = JOINT ? 2 : 1;
+  constexpr int NP = 2;
   constexpr int NJ = K_MAX / 128;
   const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
+  if (warp >= rows * batch) return;
   const int row = warp % rows;
-  const int b = (warp / rows) % batch;
-  const int w2 = warp / (rows * batch);
-  if (w2 >= (JOINT ? 1 : 2)) return;
+  const int b = warp / rows;
   if (skip && skip[b]) return;
-  const int part0 = JOINT ? 0 : w2;
+  const int part0 = 0;
   double v[NP][NJ][4];
   unsigned long long mx = 0;  // largest |x| of the row(s), compared on the bit patterns (sign cleared)
 #pragma unroll
@@ -205,8 +205,8 @@ struct OzArgs {
   int Kp;         // K padded to KP_ALIGN
   int batch;
   int S;          // digits per operand in the digit arrays (their layout)
-  int Su;         // leading digits used (<= S): pairs s, t <= Su with s + t <= Su + 1
-  const int* expA;  // [2][batch][n]
+  int Su;         // leading digits used (<= S, 2..8): pairs s, t <= Su with s + t <= Su + 1
+  const int* expA;  // [2][batch][n] (joint: equal for both parts)
   const int* expB;  // [2][batch][n]
   // RESID: RT planes (re, im): R^T, plus per-matrix sum of squares
   double* outR;     // [2][batch][n][n]
@@ -226,19 +226,23 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float e = (hi - (s - bb)) + (x - bb);
-  hi = s;
-  lo += e;
-}
+// The pair schedule shared by the producer and the MMA issuer: for each term,
+// band, digit s of A (with a non-empty run of B digits t in the band), K chunk
+// ch, and t in the run.  Band b covers weights w = s + t in [lo(b), hi(b)].
+__device__ __forceinline__ int band_lo(int band) { return band ? 6 : 2; }
+__device__ __forceinline__ int band_hi(int band, int Su) { return band ? Su + 1 : (Su + 1 < 5 ? Su + 1 : 5); }
 
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     oz_cgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs args) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smraw[];
+  const int n = args.n, S = args.S, batch = args.batch, Su = args.Su;
+  const int b = blockIdx.z >> 1;
+  const int part = blockIdx.z & 1;  // 0: real part of the product, 1: imaginary part
+  // a converged or failed matrix: the whole CTA leaves before it allocates TMEM
+  if (args.skip && args.skip[b]) return;
+
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   unsigned char* a_res = base;
   unsigned char* b_ring = base + A_RES_BYTES;
@@ -247,35 +251,33 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* b_empty = bars + B_STAGES;
   uint64_t* a_full = bars + 2 * B_STAGES;  // [2]
   uint64_t* a_empty = a_full + 2;          // [2]
-  uint64_t* term_done = a_empty + 2;
-  uint64_t* drained = term_done + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
+  uint64_t* slot_full = a_empty + 2;       // [SLOTS]: group complete (MMA -> epilogue)
+  uint64_t* slot_empty = slot_full + SLOTS;  // [SLOTS]: group drained (epilogue -> MMA)
+  uint64_t* mma_done = slot_empty + SLOTS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = args.n, S = args.S, batch = args.batch;
-  const int Su = args.Su;
-  const int b = blockIdx.z >> 1;
-  const int part = blockIdx.z & 1;  // 0: real part of the product, 1: imaginary part
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nkb = args.Kp / KB;
-  // a converged or failed matrix: the whole CTA leaves before it allocates TMEM
-  if (args.skip && args.skip[b]) return;
+  const int nch = args.Kp / (KB * CHUNK_KB);
   // terms: (A operand part, B operand part, sign)
   const int ta0 = 0, tb0 = part;              // Ar Br (re) / Ar Bi (im)
   const int ta1 = 1, tb1 = part ^ 1;          // Ai Bi (re) / Ai Br (im)
   const float sg1 = part == 0 ? -1.f : 1.f;   // - Ai Bi (re), + Ai Br (im)
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < B_STAGES; ++s) {
-      mbar_init(&b_full[s], 1);
-      mbar_init(&b_empty[s], 1);
+    for (int i = 0; i < B_STAGES; ++i) {
+      mbar_init(&b_full[i], 1);
+      mbar_init(&b_empty[i], 1);
     }
-    mbar_init(&a_full[0], 1);
-    mbar_init(&a_full[1], 1);
-    mbar_init(&a_empty[0], 1);
-    mbar_init(&a_empty[1], 1);
-    mbar_init(term_done, 1);
-    mbar_init(drained, 4);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&a_full[i], 1);
+      mbar_init(&a_empty[i], 1);
+    }
+    for (int i = 0; i < SLOTS; ++i) {
+      mbar_init(&slot_full[i], 1);
+      mbar_init(&slot_empty[i], EPI_WARPS);
+    }
+    mbar_init(mma_done, 1);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -287,206 +289,180 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  {
-    if (warp == 0 && lane == 0) {
-      // ---------------- producer
-      const int nch = (nkb + A_CHUNK_KB - 1) / A_CHUNK_KB;
-      int bi = 0;   // B stage fill counter
-      int ai = 0;   // A chunk fill counter
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer: A chunks and B stages in schedule order
+      int bi = 0, ai = 0;
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
         const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
-        for (int s = 1; s <= Su && ok; ++s) {
-          const int za = (ap * S + (s - 1)) * batch + b;
-          for (int ch = 0; ch < nch && ok; ++ch) {
-            const int kb0 = ch * A_CHUNK_KB;
-            const int kb1 = (kb0 + A_CHUNK_KB < nkb) ? kb0 + A_CHUNK_KB : nkb;
-            const int slot = ai & 1;
-            if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
-            mbar_arrive_expect_tx(&a_full[slot], (uint32_t)((kb1 - kb0) * BM * KB * 2));
-            unsigned char* abuf = a_res + slot * A_CHUNK_BYTES;
-            for (int kb = kb0; kb < kb1; ++kb)
-              tma_load_3d(abuf + (kb - kb0) * (BM * KB * 2), &mapA, &a_full[slot], kb * KB, m0, za);
-            ++ai;
-            for (int t = 1; t <= Su + 1 - s && ok; ++t) {
-              const int zb = (bp * S + (t - 1)) * batch + b;
-              for (int kb = kb0; kb < kb1; kb += KSTAGE) {
+        for (int band = 0; band < 2 && ok; ++band) {
+          const int lo = band_lo(band), hi = band_hi(band, Su);
+          for (int s = 1; s <= Su && ok; ++s) {
+            const int tlo = lo - s > 1 ? lo - s : 1;
+            const int thi = hi - s < Su ? hi - s : Su;
+            if (tlo > thi) continue;
+            const int za = (ap * S + (s - 1)) * batch + b;
+            for (int ch = 0; ch < nch && ok; ++ch) {
+              const int slot = ai & 1;
+              if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
+              mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
+#pragma unroll
+              for (int q = 0; q < CHUNK_KB; ++q)
+                tma_load_3d(a_res + slot * A_CHUNK_BYTES + q * A_BOX_BYTES, &mapA, &a_full[slot],
+                            (ch * CHUNK_KB + q) * KB, m0, za);
+              ++ai;
+              for (int t = tlo; t <= thi && ok; ++t) {
+                const int zb = (bp * S + (t - 1)) * batch + b;
                 const int st = bi % B_STAGES;
                 if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
-                mbar_arrive_expect_tx(&b_full[st], B_STAGE_BYTES);
+                mbar_arrive_expect_tx(&b_full[st], (uint32_t)B_STAGE_BYTES);
 #pragma unroll
-                for (int q = 0; q < KSTAGE; ++q)
-                  tma_load_3d(b_ring + st * B_STAGE_BYTES + q * B_BOX_BYTES, &mapB, &b_full[st], (kb + q) * KB, n0, zb);
+                for (int q = 0; q < CHUNK_KB; ++q)
+                  tma_load_3d(b_ring + st * B_STAGE_BYTES + q * B_BOX_BYTES, &mapB, &b_full[st],
+                              (ch * CHUNK_KB + q) * KB, n0, zb);
                 ++bi;
               }
             }
           }
         }
       }
-      if (!ok) atomicExch(args.err, FROB_ERR_TIMEOUT);
-    } else if (warp == 1 && lane == 0) {
+      if (!ok) {
+        atomicExch(args.err, FROB_ERR_TIMEOUT);
+        // let the copies already issued land before the CTA can leave
+        for (int j = (bi > B_STAGES ? bi - B_STAGES : 0); j < bi; ++j)
+          mbar_wait(&b_full[j % B_STAGES], (j / B_STAGES) & 1);
+        for (int j = (ai > 2 ? ai - 2 : 0); j < ai; ++j) mbar_wait(&a_full[j & 1], (j >> 1) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t IDESC = instr_desc<0, BN>();
-      const int nch = (nkb + A_CHUNK_KB - 1) / A_CHUNK_KB;
       int bi = 0, ai = 0;
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
-        if (term == 1 && !mbar_wait(drained, 0)) { ok = false; break; }  // groups drained after term 0
-        tc_fence_after();
-        uint32_t started = 0;
-        for (int s = 1; s <= Su && ok; ++s) {
-          for (int ch = 0; ch < nch && ok; ++ch) {
-            const int kb0 = ch * A_CHUNK_KB;
-            const int kb1 = (kb0 + A_CHUNK_KB < nkb) ? kb0 + A_CHUNK_KB : nkb;
-            const int slot = ai & 1;
-            if (!mbar_wait(&a_full[slot], (ai >> 1) & 1)) { ok = false; break; }
-            ++ai;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(a_res + slot * A_CHUNK_BYTES);
-            for (int t = 1; t <= Su + 1 - s && ok; ++t) {
-              const int g = group_of(s, t);
-              const uint32_t dt = tmem + (uint32_t)(g * BN);
-              for (int kb = kb0; kb < kb1; kb += KSTAGE) {
+        uint32_t started = 0;  // weights of this term whose accumulator has been initialised
+        for (int band = 0; band < 2 && ok; ++band) {
+          const int lo = band_lo(band), hi = band_hi(band, Su);
+          for (int s = 1; s <= Su && ok; ++s) {
+            const int tlo = lo - s > 1 ? lo - s : 1;
+            const int thi = hi - s < Su ? hi - s : Su;
+            if (tlo > thi) continue;
+            for (int ch = 0; ch < nch && ok; ++ch) {
+              const int aslot = ai & 1;
+              if (!mbar_wait(&a_full[aslot], (ai >> 1) & 1)) { ok = false; break; }
+              ++ai;
+              tc_fence_after();
+              const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
+              for (int t = tlo; t <= thi && ok; ++t) {
+                const int w = s + t;
+                const int g = term * Su + (w - 2);  // group index in the tile
+                const int slot = g % SLOTS;
+                if (ch == 0 && !((started >> w) & 1u) && g >= SLOTS) {
+                  // first MMA into this slot for group g: wait until group g - SLOTS is drained
+                  if (!mbar_wait(&slot_empty[slot], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
+                  tc_fence_after();
+                }
                 const int st = bi % B_STAGES;
                 if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
+                const uint32_t dt = tmem + (uint32_t)(slot * BN);
 #pragma unroll
-                for (int q = 0; q < KSTAGE; ++q)
+                for (int q = 0; q < CHUNK_KB; ++q)
 #pragma unroll
                   for (int kk = 0; kk < KB / 16; ++kk) {
-                    const uint64_t ad = sw128_desc(sa + (kb + q - kb0) * (BM * KB * 2) + kk * 32);
+                    const uint64_t ad = sw128_desc(sa + q * A_BOX_BYTES + kk * 32);
                     const uint64_t bd = sw128_desc(sb + q * B_BOX_BYTES + kk * 32);
-                    const uint32_t acc = ((started >> g) & 1u) ? 1u : 0u;
-                    mma<0>(dt, ad, bd, IDESC, acc);
-                    started |= 1u << g;
+                    mma<0>(dt, ad, bd, IDESC, ((started >> w) & 1u));
+                    started |= 1u << w;
                   }
                 mma_commit(&b_empty[st]);
                 ++bi;
               }
+              mma_commit(&a_empty[aslot]);  // chunk buffer free once these MMAs complete
             }
-            mma_commit(&a_empty[slot]);  // chunk buffer free once these MMAs complete
+            // groups whose last pair was digit s of A are complete
+            if (ok)
+              for (int t = tlo; t <= thi; ++t) {
+                const int w = s + t;
+                const int slast = w - 1 < Su ? w - 1 : Su;
+                if (s == slast) mma_commit(&slot_full[(term * Su + (w - 2)) % SLOTS]);
+              }
           }
         }
-        mma_commit(term_done);  // phase `term` of term_done
       }
       if (!ok) atomicExch(args.err, FROB_ERR_TIMEOUT);
-    } else if (warp >= 2) {
-      // ---------------- epilogue: warps 2..5 -> TMEM lanes 32 (warp % 4) ..
-      const int sub = warp & 3;
-      const int row = m0 + sub * 32 + lane;
-      const int ngroups = Su;  // weights 2 .. Su + 1
-      int* colexp = reinterpret_cast<int*>(tmem_slot + 4) + sub * BN;  // this warp's column exponents
-      const int64_t nn = (int64_t)n * n;
-      bool ok = true;
-      if constexpr (MODE == RESID) {
-        // Exact accumulation: both terms share the row and column exponents
-        // (joint splits), every group value is an integer in FP32, and the
-        // sum over groups and terms is kept in 64-bit fixed point, in units of
-        // 2^-52 of the scaled product (|scaled product| < 2^11).  Groups of
-        // weight 2^-56 and 2^-63 are rounded to that unit (at most 2^-53).
-        long long acc[BN];
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0);  // every MMA of this CTA has finished with TMEM and shared memory
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9 -> TMEM lanes 32 (warp % 4) .., column half
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
+    long long acc[64];
 #pragma unroll
-        for (int c = 0; c < BN; ++c) acc[c] = 0;
-        for (int term = 0; term < 2; ++term) {
-          if (!mbar_wait(term_done, term)) { ok = false; break; }
-          tc_fence_after();
-          const float sgn = term ? sg1 : 1.f;
-          for (int g = 0; g < ngroups; ++g) {
-            const int sh = 52 - 7 * weight_of_group(g);
-            const float pre = sh < 0 ? sgn * pow2f(sh) : sgn;
-            const int lsh = sh < 0 ? 0 : sh;
+    for (int c = 0; c < 64; ++c) acc[c] = 0;
+    bool ok = true;
+    const int ngroups = 2 * Su;
+    for (int g = 0; g < ngroups; ++g) {
+      const int slot = g % SLOTS;
+      if (!mbar_wait(&slot_full[slot], (g / SLOTS) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const int term = g / Su;
+      const int w = g % Su + 2;
+      const float sgn = term ? sg1 : 1.f;
+      const int sh = 52 - 7 * w;
+      const float pre = sh < 0 ? sgn * pow2f(sh) : sgn;
+      const int lsh = sh < 0 ? 0 : sh;
 #pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-              float v[16];
-              tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * BN + c0), v);
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + (uint32_t)(slot * BN + c0), v);
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                acc[c0 + i] += (long long)((unsigned long long)(long long)__float2int_rn(v[i] * pre) << lsh);
-            }
-          }
-          __syncwarp();
-          tc_fence_before();
-          __syncwarp();
-          if (term == 0 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(drained)) : "memory");
-        }
-        if (!ok && lane == 0) atomicExch(args.err, FROB_ERR_TIMEOUT);
-        for (int c = lane; c < BN; c += 32) {
-          const int col = n0 + c;
-          colexp[c] = col < n ? args.expB[((int64_t)tb0 * batch + b) * n + col] : 0;
-        }
-        __syncwarp();
-        const int ea = row < n ? args.expA[((int64_t)ta0 * batch + b) * n + row] : 0;
-        double ss = 0.0;  // every lane takes part in the reduction below
-        if (ok && row < n) {
-          double* RT = args.outR + ((int64_t)part * batch + b) * nn;
+        for (int i = 0; i < 16; ++i)
+          acc[c0 + i] += (long long)((unsigned long long)(long long)__float2int_rn(v[i] * pre) << lsh);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&slot_empty[slot])) : "memory");
+    }
+    if (!ok && lane == 0) atomicExch(args.err, FROB_ERR_TIMEOUT);
+    const int64_t nn = (int64_t)n * n;
+    const int ea = row < n ? args.expA[((int64_t)ta0 * batch + b) * n + row] : 0;
+    const int* eB = args.expB + ((int64_t)tb0 * batch + b) * n;
+    const int c_base = n0 + half * 64;
+    if constexpr (MODE == RESID) {
+      double ss = 0.0;  // every lane takes part in the reduction below
+      if (ok && row < n) {
+        double* RT = args.outR + ((int64_t)part * batch + b) * nn;
 #pragma unroll
-          for (int c = 0; c < BN; ++c) {
-            const int col = n0 + c;
-            if (col < n) {
-              const double pr = ldexp((double)acc[c], ea + colexp[c] - 52);
-              const double r = (part == 0 && col == row ? 1.0 : 0.0) - pr;
-              RT[(int64_t)col * n + row] = r;
-              ss += r * r;
-            }
+        for (int c = 0; c < 64; ++c) {
+          const int col = c_base + c;
+          if (col < n) {
+            const double pr = ldexp((double)acc[c], ea + __ldg(eB + col) - 52);
+            const double r = (part == 0 && col == row ? 1.0 : 0.0) - pr;
+            RT[(int64_t)col * n + row] = r;
+            ss += r * r;
           }
         }
+      }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
-      } else {
-        // float-float (hi + lo) accumulation with error-free two-sums; the
-        // terms carry their own row and column scales
-        float hi[BN], lo[BN];
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
+    } else if (ok && row < n) {
+      double* Xp = args.X + ((int64_t)part * batch + b) * nn;
+      double* XTp = args.XT + ((int64_t)part * batch + b) * nn;
 #pragma unroll
-        for (int c = 0; c < BN; ++c) {
-          hi[c] = 0.f;
-          lo[c] = 0.f;
-        }
-        float* colscale = reinterpret_cast<float*>(colexp);
-        for (int term = 0; term < 2; ++term) {
-          if (!mbar_wait(term_done, term)) { ok = false; break; }
-          tc_fence_after();
-          const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
-          const float sgn = term ? sg1 : 1.f;
-          // column scales 2^(e_B[col]) of this term, staged in shared memory
-          for (int c = lane; c < BN; c += 32) {
-            const int col = n0 + c;
-            const int eb = col < n ? args.expB[((int64_t)bp * batch + b) * n + col] : 0;
-            colscale[c] = pow2f(eb);
-          }
-          __syncwarp();
-          const int ea = row < n ? args.expA[((int64_t)ap * batch + b) * n + row] : 0;
-          for (int g = 0; g < ngroups; ++g) {
-            const int w = weight_of_group(g);
-            // sign x 2^(e_A - 7 w): exact power of two (within FP32 range for the data seen here)
-            const float rs = sgn * pow2f(ea - 7 * w);
-#pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-              float v[16];
-              tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * BN + c0), v);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) two_sum(hi[c0 + i], lo[c0 + i], (v[i] * rs) * colscale[c0 + i]);
-            }
-          }
-          __syncwarp();
-          tc_fence_before();
-          __syncwarp();
-          if (term == 0 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(drained)) : "memory");
-        }
-        if (!ok && lane == 0) atomicExch(args.err, FROB_ERR_TIMEOUT);
-        if (ok && row < n) {
-          double* Xp = args.X + ((int64_t)part * batch + b) * nn;
-          double* XTp = args.XT + ((int64_t)part * batch + b) * nn;
-#pragma unroll
-          for (int c = 0; c < BN; ++c) {
-            const int col = n0 + c;
-            if (col < n) {
-              const double v = Xp[(int64_t)row * n + col] + ((double)hi[c] + (double)lo[c]);
-              Xp[(int64_t)row * n + col] = v;
-              XTp[(int64_t)col * n + row] = v;
-            }
-          }
+      for (int c = 0; c < 64; ++c) {
+        const int col = c_base + c;
+        if (col < n) {
+          const double v = Xp[(int64_t)row * n + col] + ldexp((double)acc[c], ea + __ldg(eB + col) - 52);
+          Xp[(int64_t)row * n + col] = v;
+          XTp[(int64_t)col * n + row] = v;
         }
       }
     }

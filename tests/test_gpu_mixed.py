@@ -85,6 +85,29 @@ def test_mixed_hpd_route_vs_oracle(F, n):
         assert metrics.forward_error(x[b], exact) <= 32 * n * kappa * U64 + 4 * np.sqrt(n) * kappa * res
 
 
+@pytest.mark.parametrize("route,n", [("frob_inv", 33), ("frob_inv", 200), ("frob_inv", 512),
+                                     ("frob_inv_hpd", 129), ("frob_inv_hpd", 512)])
+def test_mixed_fine_tolerance(F, route, n):
+    """A tolerance below 1e-14 selects 8-digit residual products (pairs
+    s + t <= 9): the refinement then reaches relative residuals near 1e-16,
+    also for the HPD workload whose large diagonal sets the row scales."""
+    batch = 2
+    if route == "frob_inv":
+        ms = W.gaussian(n, batch=batch, seed=9100 + n)
+    else:
+        ms = W.hpd(n, batch=batch, seed=9200 + n)
+    r = getattr(F, route)(torch.from_numpy(ms).cuda(), prec="mixed_bf16", ns_tol=1e-15)
+    x = r.x.cpu().numpy()
+    info = r.info()
+    for b in range(batch):
+        res = metrics.residual_fro(ms[b], x[b])
+        assert info["residual"][b] <= 1e-15
+        assert res <= 2e-15, res
+        ref = oracle.cplx_lu_inv(ms[b])
+        kappa = np.linalg.cond(ms[b])
+        assert metrics.forward_error(x[b], ref) <= 32 * n * kappa * U64
+
+
 def test_mixed_reports_failure_instead_of_wrong_result(F):
     """kappa(M) ~ 2e6 with S = (1 - s^2) I: the FP32 start cannot resolve S.
     Every matrix is either refined to the FP64 target or reported
