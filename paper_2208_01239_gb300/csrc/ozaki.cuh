@@ -29,13 +29,14 @@
 // tensor pipe spends about the same time on a 128 x 64 x 16 MMA as on a
 // 128 x 128 x 16 one, so the tile is 128 wide; TMEM (512 columns) then holds
 // four 128-column accumulator slots, fewer than the up to 8 groups of a term.
-// The groups are therefore issued in two bands, weights 2..5 and 6..S+1, each
-// of at most four groups; within a band the pairs go digit s of A outermost,
-// so that a group's last pair (largest s) comes early for the heavy weights
-// and every group is complete, and drained by the epilogue warps, while the
-// tensor core works on later groups.  Group g of the tile (both terms, in
-// order) lives in slot g mod 4; an MMA into a slot waits until the epilogue
-// has drained the group that held it before.  Operands: for each digit s of A
+// The groups are therefore issued in bands of four weights, {2 .. 5} and
+// {6 .. S + 1}; group g of the tile (per term and weight, in order) lives in
+// slot g mod 4, and its first MMA waits until the epilogue has drained group
+// g - 4.  Within a band the pairs go digit s of A outermost, so that each
+// group's last pair (its largest s) comes in order of weight and the groups
+// complete, and are drained, one after another while the tensor core works on
+// the rest of the band.
+// Operands: for each digit s of A
 // and each 128-wide K chunk, the 128 x 128 chunk of the digit slice stays in
 // shared memory (double buffered) while the matching chunks of the B digit
 // slices t of the band stream through a 5-stage TMA ring (8 MMAs per stage).
@@ -226,11 +227,47 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
+// x 2^e as an FP64 number (round to nearest even), with integer operations
+// only (the FP64 pipe of this GPU retires about two lanes per clock per SM,
+// so FP64 conversions in an epilogue would idle the tensor core).  |x| < 2^63;
+// results below the normal range flush to zero.  The FP32 value (truncated,
+// for sums of squares) is returned in *f.
+__device__ __forceinline__ double i64_ldexp(long long x, int e, float* f) {
+  if (x == 0) {
+    *f = 0.f;
+    return 0.0;
+  }
+  const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                     // leading bit at 63
+  int be = 63 - lz + e + 1023;                  // biased exponent of the leading bit
+  const int fe = be - 1023 + 127;
+  *f = fe <= 0 ? 0.f : (fe >= 255 ? __int_as_float(0x7F800000) : __int_as_float((fe << 23) | (int)((m >> 40) & 0x7FFFFF)));
+  unsigned long long q = m >> 11;               // 53 bits
+  const unsigned long long rem = m & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (q & 1ull))) q += 1;
+  if (q >> 53) {
+    q >>= 1;
+    be += 1;
+  }
+  if (be <= 0) return __longlong_as_double((long long)sign);
+  if (be >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (q & 0xFFFFFFFFFFFFFull)));
+}
+
 // The pair schedule shared by the producer and the MMA issuer: for each term,
 // band, digit s of A (with a non-empty run of B digits t in the band), K chunk
-// ch, and t in the run.  Band b covers weights w = s + t in [lo(b), hi(b)].
-__device__ __forceinline__ int band_lo(int band) { return band ? 6 : 2; }
-__device__ __forceinline__ int band_hi(int band, int Su) { return band ? Su + 1 : (Su + 1 < 5 ? Su + 1 : 5); }
+// ch, and t in the run.  Band b covers the weights w = s + t in
+// [2 + W b, min(1 + W (b + 1), Su + 1)], W = BAND_W.  Group g = term Su + w - 2
+// of the tile (one per weight and term) lives in TMEM slot g mod 4, so a
+// group's first MMA waits until the epilogue has drained group g - 4.
+constexpr int BAND_W = 4;
+__device__ __forceinline__ int num_bands(int Su) { return (Su + BAND_W - 1) / BAND_W; }
+__device__ __forceinline__ int band_lo(int band) { return 2 + BAND_W * band; }
+__device__ __forceinline__ int band_hi(int band, int Su) {
+  return 1 + BAND_W * (band + 1) < Su + 1 ? 1 + BAND_W * (band + 1) : Su + 1;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -296,7 +333,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       for (int term = 0; term < 2 && ok; ++term) {
         const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
-        for (int band = 0; band < 2 && ok; ++band) {
+        for (int band = 0; band < num_bands(Su) && ok; ++band) {
           const int lo = band_lo(band), hi = band_hi(band, Su);
           for (int s = 1; s <= Su && ok; ++s) {
             const int tlo = lo - s > 1 ? lo - s : 1;
@@ -341,10 +378,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t IDESC = instr_desc<0, BN>();
       int bi = 0, ai = 0;
       bool ok = true;
+      const int nb = num_bands(Su);
       for (int term = 0; term < 2 && ok; ++term) {
-        uint32_t started = 0;  // weights of this term whose accumulator has been initialised
-        for (int band = 0; band < 2 && ok; ++band) {
+        for (int band = 0; band < nb && ok; ++band) {
           const int lo = band_lo(band), hi = band_hi(band, Su);
+          uint32_t started = 0;  // weights of this band whose accumulator has been initialised
           for (int s = 1; s <= Su && ok; ++s) {
             const int tlo = lo - s > 1 ? lo - s : 1;
             const int thi = hi - s < Su ? hi - s : Su;
@@ -357,18 +395,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
               for (int t = tlo; t <= thi && ok; ++t) {
                 const int w = s + t;
-                const int g = term * Su + (w - 2);  // group index in the tile
-                const int slot = g % SLOTS;
-                if (ch == 0 && !((started >> w) & 1u) && g >= SLOTS) {
-                  // first MMA into this slot for group g: wait until group g - SLOTS is drained
-                  if (!mbar_wait(&slot_empty[slot], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
+                const int g = term * Su + (w - 2);
+                if (!((started >> w) & 1u) && g >= SLOTS) {
+                  // first MMA of group g: slot g mod 4 must be drained of group g - 4
+                  if (!mbar_wait(&slot_empty[g % SLOTS], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
                   tc_fence_after();
                 }
                 const int st = bi % B_STAGES;
                 if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
-                const uint32_t dt = tmem + (uint32_t)(slot * BN);
+                const uint32_t dt = tmem + (uint32_t)((g % SLOTS) * BN);
 #pragma unroll
                 for (int q = 0; q < CHUNK_KB; ++q)
 #pragma unroll
@@ -407,8 +444,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int c = 0; c < 64; ++c) acc[c] = 0;
     bool ok = true;
-    const int ngroups = 2 * Su;
-    for (int g = 0; g < ngroups; ++g) {
+    for (int g = 0; g < 2 * Su; ++g) {  // groups complete in this order
       const int slot = g % SLOTS;
       if (!mbar_wait(&slot_full[slot], (g / SLOTS) & 1)) { ok = false; break; }
       tc_fence_after();
@@ -436,20 +472,31 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int* eB = args.expB + ((int64_t)tb0 * batch + b) * n;
     const int c_base = n0 + half * 64;
     if constexpr (MODE == RESID) {
-      double ss = 0.0;  // every lane takes part in the reduction below
+      // R = I - P: off the diagonal the sign bit of P flips; the diagonal
+      // (one entry per row) takes an FP64 subtraction.  sum |R_ij|^2 is
+      // accumulated in FP32 (a norm for the stopping test).
+      float ssf = 0.f;
+      double ssd = 0.0;
       if (ok && row < n) {
         double* RT = args.outR + ((int64_t)part * batch + b) * nn;
 #pragma unroll
         for (int c = 0; c < 64; ++c) {
           const int col = c_base + c;
           if (col < n) {
-            const double pr = ldexp((double)acc[c], ea + __ldg(eB + col) - 52);
-            const double r = (part == 0 && col == row ? 1.0 : 0.0) - pr;
-            RT[(int64_t)col * n + row] = r;
-            ss += r * r;
+            float pf;
+            const double pr = i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
+            if (part == 0 && col == row) {
+              const double r = 1.0 - pr;
+              RT[(int64_t)col * n + row] = r;
+              ssd += r * r;
+            } else {
+              RT[(int64_t)col * n + row] = __longlong_as_double(__double_as_longlong(pr) ^ (1ll << 63));
+              ssf = fmaf(pf, pf, ssf);
+            }
           }
         }
       }
+      double ss = ssd + (double)ssf;  // every lane takes part in the reduction below
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
@@ -460,7 +507,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int c = 0; c < 64; ++c) {
         const int col = c_base + c;
         if (col < n) {
-          const double v = Xp[(int64_t)row * n + col] + ldexp((double)acc[c], ea + __ldg(eB + col) - 52);
+          float pf;
+          const double v = Xp[(int64_t)row * n + col] + i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
           Xp[(int64_t)row * n + col] = v;
           XTp[(int64_t)col * n + row] = v;
         }
