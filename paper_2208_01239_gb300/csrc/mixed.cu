@@ -194,7 +194,12 @@ void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs
     cudaFuncSetAttribute(oz::oz_cgemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
     attr = true;
   }
-  dim3 grid((a.n + oz::BN - 1) / oz::BN, (a.n + tc::BM - 1) / tc::BM, 2 * a.batch);
+  // persistent: one CTA per SM (the shared memory admits no second), at most one per tile
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)((a.n + oz::BN - 1) / oz::BN) * ((a.n + tc::BM - 1) / tc::BM) * 2 * a.batch;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
   FROB_LAUNCH(MODE == oz::RESID ? "oz_cgemm<resid>" : "oz_cgemm<corr>", st,
               oz::oz_cgemm_kernel<MODE><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ma, mb, a));
 }

@@ -25,7 +25,7 @@
 // each output part is two real terms, and with the joint exponents both
 // terms carry the same row and column scales.
 //
-// Kernel (oz_cgemm_kernel): one 128 x 128 tile of one part per CTA.  The
+// Kernel (oz_cgemm_kernel): 128 x 128 tiles of one part, persistent CTAs.  The
 // tensor pipe spends about the same time on a 128 x 64 x 16 MMA as on a
 // 128 x 128 x 16 one, so the tile is 128 wide; TMEM (512 columns) then holds
 // four 128-column accumulator slots, fewer than the up to 8 groups of a term.
@@ -269,16 +269,35 @@ __device__ __forceinline__ int band_hi(int band, int Su) {
   return 1 + BAND_W * (band + 1) < Su + 1 ? 1 + BAND_W * (band + 1) : Su + 1;
 }
 
+// Tiles of the launch: t -> (x tile, y tile, z = 2 b + part), x fastest.
+struct TileIdx {
+  int b, part, m0, n0;
+};
+__device__ __forceinline__ TileIdx tile_of(int t, int nx, int ny) {
+  TileIdx r;
+  const int xt = t % nx;
+  const int rest = t / nx;
+  const int yt = rest % ny;
+  const int z = rest / ny;
+  r.b = z >> 1;
+  r.part = z & 1;
+  r.m0 = yt * tc::BM;
+  r.n0 = xt * BN;
+  return r;
+}
+
+// Persistent: CTA c takes tiles c, c + gridDim.x, ...; tiles of converged or
+// failed matrices are skipped by every role alike.  The pipelines (A chunks,
+// B stages, TMEM slots) run on across tiles, so the epilogue's final stores of
+// one tile overlap the MMAs of the next.
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     oz_cgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs args) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int n = args.n, S = args.S, batch = args.batch, Su = args.Su;
-  const int b = blockIdx.z >> 1;
-  const int part = blockIdx.z & 1;  // 0: real part of the product, 1: imaginary part
-  // a converged or failed matrix: the whole CTA leaves before it allocates TMEM
-  if (args.skip && args.skip[b]) return;
+  const int nx = (n + BN - 1) / BN, ny = (n + BM - 1) / BM;
+  const int ntiles = nx * ny * 2 * batch;
 
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   unsigned char* a_res = base;
@@ -294,12 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nch = args.Kp / (KB * CHUNK_KB);
-  // terms: (A operand part, B operand part, sign)
-  const int ta0 = 0, tb0 = part;              // Ar Br (re) / Ar Bi (im)
-  const int ta1 = 1, tb1 = part ^ 1;          // Ai Bi (re) / Ai Br (im)
-  const float sg1 = part == 0 ? -1.f : 1.f;   // - Ai Bi (re), + Ai Br (im)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < B_STAGES; ++i) {
@@ -331,34 +345,38 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- producer: A chunks and B stages in schedule order
       int bi = 0, ai = 0;
       bool ok = true;
-      for (int term = 0; term < 2 && ok; ++term) {
-        const int ap = term ? ta1 : ta0, bp = term ? tb1 : tb0;
-        for (int band = 0; band < num_bands(Su) && ok; ++band) {
-          const int lo = band_lo(band), hi = band_hi(band, Su);
-          for (int s = 1; s <= Su && ok; ++s) {
-            const int tlo = lo - s > 1 ? lo - s : 1;
-            const int thi = hi - s < Su ? hi - s : Su;
-            if (tlo > thi) continue;
-            const int za = (ap * S + (s - 1)) * batch + b;
-            for (int ch = 0; ch < nch && ok; ++ch) {
-              const int slot = ai & 1;
-              if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
-              mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
-#pragma unroll
-              for (int q = 0; q < CHUNK_KB; ++q)
-                tma_load_3d(a_res + slot * A_CHUNK_BYTES + q * A_BOX_BYTES, &mapA, &a_full[slot],
-                            (ch * CHUNK_KB + q) * KB, m0, za);
-              ++ai;
-              for (int t = tlo; t <= thi && ok; ++t) {
-                const int zb = (bp * S + (t - 1)) * batch + b;
-                const int st = bi % B_STAGES;
-                if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
-                mbar_arrive_expect_tx(&b_full[st], (uint32_t)B_STAGE_BYTES);
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const TileIdx T = tile_of(tile, nx, ny);
+        if (args.skip && args.skip[T.b]) continue;
+        for (int term = 0; term < 2 && ok; ++term) {
+          const int ap = term, bp = term ? (T.part ^ 1) : T.part;
+          for (int band = 0; band < num_bands(Su) && ok; ++band) {
+            const int lo = band_lo(band), hi = band_hi(band, Su);
+            for (int s = 1; s <= Su && ok; ++s) {
+              const int tlo = lo - s > 1 ? lo - s : 1;
+              const int thi = hi - s < Su ? hi - s : Su;
+              if (tlo > thi) continue;
+              const int za = (ap * S + (s - 1)) * batch + T.b;
+              for (int ch = 0; ch < nch && ok; ++ch) {
+                const int slot = ai & 1;
+                if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
+                mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
 #pragma unroll
                 for (int q = 0; q < CHUNK_KB; ++q)
-                  tma_load_3d(b_ring + st * B_STAGE_BYTES + q * B_BOX_BYTES, &mapB, &b_full[st],
-                              (ch * CHUNK_KB + q) * KB, n0, zb);
-                ++bi;
+                  tma_load_3d(a_res + slot * A_CHUNK_BYTES + q * A_BOX_BYTES, &mapA, &a_full[slot],
+                              (ch * CHUNK_KB + q) * KB, T.m0, za);
+                ++ai;
+                for (int t = tlo; t <= thi && ok; ++t) {
+                  const int zb = (bp * S + (t - 1)) * batch + T.b;
+                  const int st = bi % B_STAGES;
+                  if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
+                  mbar_arrive_expect_tx(&b_full[st], (uint32_t)B_STAGE_BYTES);
+#pragma unroll
+                  for (int q = 0; q < CHUNK_KB; ++q)
+                    tma_load_3d(b_ring + st * B_STAGE_BYTES + q * B_BOX_BYTES, &mapB, &b_full[st],
+                                (ch * CHUNK_KB + q) * KB, T.n0, zb);
+                  ++bi;
+                }
               }
             }
           }
@@ -377,58 +395,64 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- MMA issuer
       constexpr uint32_t IDESC = instr_desc<0, BN>();
       int bi = 0, ai = 0;
+      int g0 = 0;  // groups of the earlier tiles of this CTA
       bool ok = true;
       const int nb = num_bands(Su);
-      for (int term = 0; term < 2 && ok; ++term) {
-        for (int band = 0; band < nb && ok; ++band) {
-          const int lo = band_lo(band), hi = band_hi(band, Su);
-          uint32_t started = 0;  // weights of this band whose accumulator has been initialised
-          for (int s = 1; s <= Su && ok; ++s) {
-            const int tlo = lo - s > 1 ? lo - s : 1;
-            const int thi = hi - s < Su ? hi - s : Su;
-            if (tlo > thi) continue;
-            for (int ch = 0; ch < nch && ok; ++ch) {
-              const int aslot = ai & 1;
-              if (!mbar_wait(&a_full[aslot], (ai >> 1) & 1)) { ok = false; break; }
-              ++ai;
-              tc_fence_after();
-              const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
-              for (int t = tlo; t <= thi && ok; ++t) {
-                const int w = s + t;
-                const int g = term * Su + (w - 2);
-                if (!((started >> w) & 1u) && g >= SLOTS) {
-                  // first MMA of group g: slot g mod 4 must be drained of group g - 4
-                  if (!mbar_wait(&slot_empty[g % SLOTS], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
-                  tc_fence_after();
-                }
-                const int st = bi % B_STAGES;
-                if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const TileIdx T = tile_of(tile, nx, ny);
+        if (args.skip && args.skip[T.b]) continue;
+        for (int term = 0; term < 2 && ok; ++term) {
+          for (int band = 0; band < nb && ok; ++band) {
+            const int lo = band_lo(band), hi = band_hi(band, Su);
+            uint32_t started = 0;  // weights of this band whose accumulator has been initialised
+            for (int s = 1; s <= Su && ok; ++s) {
+              const int tlo = lo - s > 1 ? lo - s : 1;
+              const int thi = hi - s < Su ? hi - s : Su;
+              if (tlo > thi) continue;
+              for (int ch = 0; ch < nch && ok; ++ch) {
+                const int aslot = ai & 1;
+                if (!mbar_wait(&a_full[aslot], (ai >> 1) & 1)) { ok = false; break; }
+                ++ai;
                 tc_fence_after();
-                const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
-                const uint32_t dt = tmem + (uint32_t)((g % SLOTS) * BN);
-#pragma unroll
-                for (int q = 0; q < CHUNK_KB; ++q)
-#pragma unroll
-                  for (int kk = 0; kk < KB / 16; ++kk) {
-                    const uint64_t ad = sw128_desc(sa + q * A_BOX_BYTES + kk * 32);
-                    const uint64_t bd = sw128_desc(sb + q * B_BOX_BYTES + kk * 32);
-                    mma<0>(dt, ad, bd, IDESC, ((started >> w) & 1u));
-                    started |= 1u << w;
+                const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
+                for (int t = tlo; t <= thi && ok; ++t) {
+                  const int w = s + t;
+                  const int g = g0 + term * Su + (w - 2);
+                  if (!((started >> w) & 1u) && g >= SLOTS) {
+                    // first MMA of group g: slot g mod 4 must be drained of group g - 4
+                    if (!mbar_wait(&slot_empty[g % SLOTS], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
+                    tc_fence_after();
                   }
-                mma_commit(&b_empty[st]);
-                ++bi;
+                  const int st = bi % B_STAGES;
+                  if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
+                  tc_fence_after();
+                  const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
+                  const uint32_t dt = tmem + (uint32_t)((g % SLOTS) * BN);
+#pragma unroll
+                  for (int q = 0; q < CHUNK_KB; ++q)
+#pragma unroll
+                    for (int kk = 0; kk < KB / 16; ++kk) {
+                      const uint64_t ad = sw128_desc(sa + q * A_BOX_BYTES + kk * 32);
+                      const uint64_t bd = sw128_desc(sb + q * B_BOX_BYTES + kk * 32);
+                      mma<0>(dt, ad, bd, IDESC, ((started >> w) & 1u));
+                      started |= 1u << w;
+                    }
+                  mma_commit(&b_empty[st]);
+                  ++bi;
+                }
+                mma_commit(&a_empty[aslot]);  // chunk buffer free once these MMAs complete
               }
-              mma_commit(&a_empty[aslot]);  // chunk buffer free once these MMAs complete
+              // groups whose last pair was digit s of A are complete
+              if (ok)
+                for (int t = tlo; t <= thi; ++t) {
+                  const int w = s + t;
+                  const int slast = w - 1 < Su ? w - 1 : Su;
+                  if (s == slast) mma_commit(&slot_full[(g0 + term * Su + (w - 2)) % SLOTS]);
+                }
             }
-            // groups whose last pair was digit s of A are complete
-            if (ok)
-              for (int t = tlo; t <= thi; ++t) {
-                const int w = s + t;
-                const int slast = w - 1 < Su ? w - 1 : Su;
-                if (s == slast) mma_commit(&slot_full[(term * Su + (w - 2)) % SLOTS]);
-              }
           }
         }
+        g0 += 2 * Su;
       }
       if (!ok) atomicExch(args.err, FROB_ERR_TIMEOUT);
       mma_commit(mma_done);
@@ -438,82 +462,93 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue: warps 2..9 -> TMEM lanes 32 (warp % 4) .., column half
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
-    const int row = m0 + quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
-    long long acc[64];
-#pragma unroll
-    for (int c = 0; c < 64; ++c) acc[c] = 0;
-    bool ok = true;
-    for (int g = 0; g < 2 * Su; ++g) {  // groups complete in this order
-      const int slot = g % SLOTS;
-      if (!mbar_wait(&slot_full[slot], (g / SLOTS) & 1)) { ok = false; break; }
-      tc_fence_after();
-      const int term = g / Su;
-      const int w = g % Su + 2;
-      const float sgn = term ? sg1 : 1.f;
-      const int sh = 52 - 7 * w;
-      const float pre = sh < 0 ? sgn * pow2f(sh) : sgn;
-      const int lsh = sh < 0 ? 0 : sh;
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float v[16];
-        tmem_ld16(lane_base + (uint32_t)(slot * BN + c0), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          acc[c0 + i] += (long long)((unsigned long long)(long long)__float2int_rn(v[i] * pre) << lsh);
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&slot_empty[slot])) : "memory");
-    }
-    if (!ok && lane == 0) atomicExch(args.err, FROB_ERR_TIMEOUT);
     const int64_t nn = (int64_t)n * n;
-    const int ea = row < n ? args.expA[((int64_t)ta0 * batch + b) * n + row] : 0;
-    const int* eB = args.expB + ((int64_t)tb0 * batch + b) * n;
-    const int c_base = n0 + half * 64;
-    if constexpr (MODE == RESID) {
-      // R = I - P: off the diagonal the sign bit of P flips; the diagonal
-      // (one entry per row) takes an FP64 subtraction.  sum |R_ij|^2 is
-      // accumulated in FP32 (a norm for the stopping test).
-      float ssf = 0.f;
-      double ssd = 0.0;
-      if (ok && row < n) {
-        double* RT = args.outR + ((int64_t)part * batch + b) * nn;
+    int g0 = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const TileIdx T = tile_of(tile, nx, ny);
+      if (args.skip && args.skip[T.b]) continue;
+      const int b = T.b, part = T.part;
+      const int row = T.m0 + quarter * 32 + lane;
+      const float sg1 = part == 0 ? -1.f : 1.f;  // - Ai Bi (re), + Ai Br (im)
+      long long acc[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) acc[c] = 0;
+      for (int gl = 0; gl < 2 * Su; ++gl) {  // groups complete in this order
+        const int g = g0 + gl;
+        const int slot = g % SLOTS;
+        if (!mbar_wait(&slot_full[slot], (g / SLOTS) & 1)) { ok = false; break; }
+        tc_fence_after();
+        const int term = gl / Su;
+        const int w = gl % Su + 2;
+        const float sgn = term ? sg1 : 1.f;
+        const int sh = 52 - 7 * w;
+        const float pre = sh < 0 ? sgn * pow2f(sh) : sgn;
+        const int lsh = sh < 0 ? 0 : sh;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + (uint32_t)(slot * BN + c0), v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            acc[c0 + i] += (long long)((unsigned long long)(long long)__float2int_rn(v[i] * pre) << lsh);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&slot_empty[slot])) : "memory");
+      }
+      g0 += 2 * Su;
+      if (!ok) break;
+      // the two terms share the row and column exponents (joint splits)
+      const int ea = row < n ? args.expA[(int64_t)b * n + row] : 0;
+      const int* eB = args.expB + ((int64_t)part * batch + b) * n;
+      const int c_base = T.n0 + half * 64;
+      if constexpr (MODE == RESID) {
+        // R = I - P: off the diagonal the sign bit of P flips; the diagonal
+        // (one entry per row) takes an FP64 subtraction.  sum |R_ij|^2 is
+        // accumulated in FP32 (a norm for the stopping test).
+        float ssf = 0.f;
+        double ssd = 0.0;
+        if (row < n) {
+          double* RT = args.outR + ((int64_t)part * batch + b) * nn;
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            const int col = c_base + c;
+            if (col < n) {
+              float pf;
+              const double pr = i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
+              if (part == 0 && col == row) {
+                const double r = 1.0 - pr;
+                RT[(int64_t)col * n + row] = r;
+                ssd += r * r;
+              } else {
+                RT[(int64_t)col * n + row] = __longlong_as_double(__double_as_longlong(pr) ^ (1ll << 63));
+                ssf = fmaf(pf, pf, ssf);
+              }
+            }
+          }
+        }
+        double ss = ssd + (double)ssf;  // every lane takes part in the reduction below
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
+      } else if (row < n) {
+        double* Xp = args.X + ((int64_t)part * batch + b) * nn;
+        double* XTp = args.XT + ((int64_t)part * batch + b) * nn;
 #pragma unroll
         for (int c = 0; c < 64; ++c) {
           const int col = c_base + c;
           if (col < n) {
             float pf;
-            const double pr = i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
-            if (part == 0 && col == row) {
-              const double r = 1.0 - pr;
-              RT[(int64_t)col * n + row] = r;
-              ssd += r * r;
-            } else {
-              RT[(int64_t)col * n + row] = __longlong_as_double(__double_as_longlong(pr) ^ (1ll << 63));
-              ssf = fmaf(pf, pf, ssf);
-            }
+            const double v = Xp[(int64_t)row * n + col] + i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
+            Xp[(int64_t)row * n + col] = v;
+            XTp[(int64_t)col * n + row] = v;
           }
         }
       }
-      double ss = ssd + (double)ssf;  // every lane takes part in the reduction below
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
-    } else if (ok && row < n) {
-      double* Xp = args.X + ((int64_t)part * batch + b) * nn;
-      double* XTp = args.XT + ((int64_t)part * batch + b) * nn;
-#pragma unroll
-      for (int c = 0; c < 64; ++c) {
-        const int col = c_base + c;
-        if (col < n) {
-          float pf;
-          const double v = Xp[(int64_t)row * n + col] + i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
-          Xp[(int64_t)row * n + col] = v;
-          XTp[(int64_t)col * n + row] = v;
-        }
-      }
     }
+    if (!ok && lane == 0) atomicExch(args.err, FROB_ERR_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
