@@ -501,39 +501,49 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
 }
 
 // Cholesky of the kb x kb diagonal block of the panel [k0, k0+kb) (lower,
-// A11 = L11 L11^H), one warp per matrix (grid: batch).  A non-positive or
-// non-finite diagonal reports FROB_ERR_NOT_HPD with bad_index =
-// k + 1 + info_off and continues with a unit pivot.
+// A11 = L11 L11^H), one warp per matrix (grid: batch).  Lane r keeps row r of
+// the block in registers; step j broadcasts column j through shared memory
+// and every lane applies its rank-1 update with independent FMAs.  A
+// non-positive or non-finite diagonal reports FROB_ERR_NOT_HPD with
+// bad_index = k + 1 + info_off and continues with a unit pivot.
 template <typename T>
 __global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int k0, int kb, MatB<T> A, frob_info* info,
                                                          int info_off) {
   using K = typename real_of<T>::type;
   const int b = blockIdx.x;
   const int lane = threadIdx.x;
-  __shared__ T D[PANEL_MAX][PANEL_MAX + 1];
+  __shared__ T colj[PANEL_MAX];
   T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
-  for (int r = 0; r < kb; ++r)
-    if (lane <= r) D[r][lane] = g[(int64_t)r * A.ld + lane];
-  __syncwarp();
+  T r[PANEL_MAX];
+#pragma unroll
+  for (int c = 0; c < PANEL_MAX; ++c) r[c] = (lane < kb && c <= lane) ? g[(int64_t)lane * A.ld + c] : zero_v<T>();
   int fail = -1;
-  for (int j = 0; j < kb; ++j) {
-    const K d = real_(D[j][j]);
-    const bool ok = d > (K)0 && d < (K)INFINITY;
-    if (!ok && fail < 0) fail = j;
-    const K l = ok ? sqrt(d) : (K)1;
-    __syncwarp();
-    if (lane == j) D[j][j] = from_real<T>(l);
-    if (lane > j && lane < kb) D[lane][j] = mul_(D[lane][j], from_real<T>((K)1 / l));
-    __syncwarp();
-    if (lane > j && lane < kb) {
-      const T lij = neg_(D[lane][j]);
-      for (int c = j + 1; c <= lane; ++c) mac(D[lane][c], lij, conj_(D[c][j]));
+#pragma unroll
+  for (int j = 0; j < PANEL_MAX; ++j) {
+    if (j < kb) {
+      colj[lane] = r[j];
+      __syncwarp();
+      const K d = real_(colj[j]);
+      const bool ok = d > (K)0 && d < (K)INFINITY;
+      if (!ok && fail < 0) fail = j;
+      const K l = ok ? sqrt(d) : (K)1;
+      __syncwarp();
+      if (lane == j) r[j] = from_real<T>(l);
+      if (lane > j) r[j] = mul_(r[j], from_real<T>((K)1 / l));  // L[lane][j]
+      colj[lane] = r[j];
+      __syncwarp();
+      const T lij = neg_(r[j]);
+#pragma unroll
+      for (int c = j + 1; c < PANEL_MAX; ++c)
+        if (c <= lane) mac(r[c], lij, conj_(colj[c]));
+      __syncwarp();
     }
-    __syncwarp();
   }
   if (fail >= 0 && lane == 0) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + fail + 1);
-  for (int r = 0; r < kb; ++r)
-    if (lane <= r) g[(int64_t)r * A.ld + lane] = D[r][lane];
+  if (lane < kb)
+#pragma unroll
+    for (int c = 0; c < PANEL_MAX; ++c)
+      if (c <= lane) g[(int64_t)lane * A.ld + c] = r[c];
 }
 
 // Rows below the diagonal block: L21 = A21 L11^{-H}, i.e. each row x solves

@@ -77,12 +77,43 @@ bool digit_map(CUtensorMap* map, const __nv_bfloat16* ptr, int n, int Kp, int S,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// M (c128) -> M32 (c64) and FP64 planes [2][batch][n][n]; ||M||_F^2 per matrix
+// Precision conversions with integer operations (this GPU's FP64 unit, which
+// also converts, retires about two lanes per clock per SM).
+// FP64 -> FP32, round to nearest even; magnitudes below the FP32 normal range
+// flush to zero, above it saturate to infinity; NaN stays NaN.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int ex = (int)((u >> 52) & 0x7FF);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  if (ex == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int e = ex - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  const unsigned q = (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1FFFFFFFull;
+  unsigned bits = e >= 255 ? 0x7F800000u : (((unsigned)e << 23) + q);
+  if (e < 255 && (rem > 0x10000000ull || (rem == 0x10000000ull && (q & 1u)))) bits += 1;  // a carry bumps the exponent
+  if (bits > 0x7F800000u) bits = 0x7F800000u;
+  return __uint_as_float(sign | bits);
+}
+// FP32 -> FP64, exact (FP32 subnormals flush to zero).
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long m = u & 0x7FFFFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long de = e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (de << 52) | (m << 29)));
+}
+
+// M (c128) -> M32 (c64) and FP64 planes [2][batch][n][n]; ||M||_F^2 per
+// matrix (FP32 partial sums, one atomic per block)
 __global__ void conv_in_kernel(int n, MatB<const zd> M, MatB<zf> M32, double* Mp, double* nM2, int hpd) {
   const int b = blockIdx.z;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nn = (int64_t)n * n;
-  double ss = 0.0;
+  float ss = 0.f;
   if (e < nn) {
     const int i = (int)(e / n), j = (int)(e % n);
     zd v;
@@ -94,13 +125,21 @@ __global__ void conv_in_kernel(int n, MatB<const zd> M, MatB<zf> M32, double* Mp
       const zd w = M.at(b)[(int64_t)j * M.ld + i];   // upper triangle from the lower one
       v = zd{w.x, -w.y};
     }
-    M32.at(b)[(int64_t)i * M32.ld + j] = zf{(float)v.x, (float)v.y};
+    const zf v32{d2f_int(v.x), d2f_int(v.y)};
+    M32.at(b)[(int64_t)i * M32.ld + j] = v32;
     Mp[(int64_t)b * nn + e] = v.x;
     Mp[((int64_t)gridDim.z + b) * nn + e] = v.y;
-    ss = v.x * v.x + v.y * v.y;
+    ss = fmaf(v32.x, v32.x, v32.y * v32.y);
   }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if ((threadIdx.x & 31) == 0 && ss != 0.0) atomicAdd(nM2 + b, ss);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float w = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0 && w != 0.f) atomicAdd(nM2 + b, (double)w);
+  }
 }
 
 // X32 (c64) -> planes X, X^T (FP64)
@@ -111,10 +150,11 @@ __global__ void conv_x_kernel(int n, MatB<const zf> X32, double* Xp, double* XTp
   if (e >= nn) return;
   const int i = (int)(e / n), j = (int)(e % n);
   const zf v = X32.at(b)[(int64_t)i * X32.ld + j];
-  Xp[(int64_t)b * nn + e] = v.x;
-  Xp[((int64_t)batch + b) * nn + e] = v.y;
-  XTp[(int64_t)b * nn + (int64_t)j * n + i] = v.x;
-  XTp[((int64_t)batch + b) * nn + (int64_t)j * n + i] = v.y;
+  const double re = f2d_int(v.x), im = f2d_int(v.y);
+  Xp[(int64_t)b * nn + e] = re;
+  Xp[((int64_t)batch + b) * nn + e] = im;
+  XTp[(int64_t)b * nn + (int64_t)j * n + i] = re;
+  XTp[((int64_t)batch + b) * nn + (int64_t)j * n + i] = im;
 }
 
 // planes X -> interleaved c128 output
@@ -140,7 +180,7 @@ __global__ void xnorm_kernel(int n, const double* Xp, double* nX2, int batch, co
   for (int k = 0; k < XN_PER_THREAD; ++k) {
     const int64_t e = e0 + (int64_t)k * blockDim.x;
     if (e < nn) {
-      const float a = (float)Xp[(int64_t)b * nn + e], c = (float)Xp[((int64_t)batch + b) * nn + e];
+      const float a = d2f_int(Xp[(int64_t)b * nn + e]), c = d2f_int(Xp[((int64_t)batch + b) * nn + e]);
       ss = fmaf(a, a, fmaf(c, c, ss));
     }
   }
@@ -187,6 +227,8 @@ __global__ void check_kernel(int batch, int it, int last, double tol, const doub
   }
 }
 
+// The digit products, persistent: one CTA per SM (the shared memory admits
+// no second), at most one per tile.
 template <int MODE>
 void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs& a, cudaStream_t st) {
   static bool attr = false;
@@ -194,11 +236,11 @@ void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs
     cudaFuncSetAttribute(oz::oz_cgemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
     attr = true;
   }
-  // persistent: one CTA per SM (the shared memory admits no second), at most one per tile
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = (int64_t)((a.n + oz::BN - 1) / oz::BN) * ((a.n + tc::BM - 1) / tc::BM) * 2 * a.batch;
+  const int64_t tiles =
+      (int64_t)((a.n + oz::BN - 1) / oz::BN) * ((a.n + tc::BM - 1) / tc::BM) * 2 * a.batch;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
   FROB_LAUNCH(MODE == oz::RESID ? "oz_cgemm<resid>" : "oz_cgemm<corr>", st,
               oz::oz_cgemm_kernel<MODE><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ma, mb, a));

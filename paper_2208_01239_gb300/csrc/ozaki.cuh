@@ -38,8 +38,8 @@
 // the rest of the band.
 // Operands: for each digit s of A
 // and each 128-wide K chunk, the 128 x 128 chunk of the digit slice stays in
-// shared memory (double buffered) while the matching chunks of the B digit
-// slices t of the band stream through a 5-stage TMA ring (8 MMAs per stage).
+// shared memory (three chunk buffers) while the matching chunks of the B digit
+// slices t of the band stream through a 4-stage TMA ring (8 MMAs per stage).
 //
 // Epilogue (8 warps; warp w reads TMEM lanes 32 (w mod 4) .. + 31 and one
 // 64-column half): each group is added, exactly, into a 64-bit fixed-point
@@ -49,6 +49,7 @@
 //           adds sum |R_ij|^2 into a per-matrix FP64 accumulator.
 //   CORR:   X <- X + A B, written to X (row-major) and X^T.
 #pragma once
+
 
 #include <cstdint>
 #include <cuda.h>
@@ -69,14 +70,15 @@ constexpr int K_MAX = 512;    // largest inner dimension with exact FP32 accumul
 constexpr int CHUNK_KB = 2;                                // k-blocks per K chunk (128 K)
 constexpr int A_BOX_BYTES = tc::BM * KB * 2;               // 16 KB
 constexpr int A_CHUNK_BYTES = A_BOX_BYTES * CHUNK_KB;      // 32 KB
-constexpr int A_RES_BYTES = 2 * A_CHUNK_BYTES;             // double-buffered
+constexpr int A_BUFS = 3;                                  // A chunk buffers
+constexpr int A_RES_BYTES = A_BUFS * A_CHUNK_BYTES;
 constexpr int B_BOX_BYTES = BN * KB * 2;                   // 16 KB
 constexpr int B_STAGE_BYTES = B_BOX_BYTES * CHUNK_KB;      // 32 KB: 8 MMAs per stage
-constexpr int B_STAGES = 5;
+constexpr int B_STAGES = 4;
 constexpr int SLOTS = 4;                                   // 128-column TMEM accumulators
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;               // producer, MMA, epilogue warps
-constexpr int NUM_BARS = 2 * B_STAGES + 4 + 2 * SLOTS + 1;
+constexpr int NUM_BARS = 2 * B_STAGES + 2 * A_BUFS + 2 * SLOTS + 1;
 constexpr int SMEM_BYTES = A_RES_BYTES + B_STAGES * B_STAGE_BYTES + 1024 + NUM_BARS * 8 + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 static_assert(KP_ALIGN == KB * CHUNK_KB, "one B stage per (digit pair, K chunk)");
@@ -305,9 +307,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(b_ring + B_STAGES * B_STAGE_BYTES);
   uint64_t* b_full = bars;
   uint64_t* b_empty = bars + B_STAGES;
-  uint64_t* a_full = bars + 2 * B_STAGES;  // [2]
-  uint64_t* a_empty = a_full + 2;          // [2]
-  uint64_t* slot_full = a_empty + 2;       // [SLOTS]: group complete (MMA -> epilogue)
+  uint64_t* a_full = bars + 2 * B_STAGES;  // [A_BUFS]
+  uint64_t* a_empty = a_full + A_BUFS;     // [A_BUFS]
+  uint64_t* slot_full = a_empty + A_BUFS;  // [SLOTS]: group complete (MMA -> epilogue)
   uint64_t* slot_empty = slot_full + SLOTS;  // [SLOTS]: group drained (epilogue -> MMA)
   uint64_t* mma_done = slot_empty + SLOTS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&b_full[i], 1);
       mbar_init(&b_empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < A_BUFS; ++i) {
       mbar_init(&a_full[i], 1);
       mbar_init(&a_empty[i], 1);
     }
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (tlo > thi) continue;
               const int za = (ap * S + (s - 1)) * batch + T.b;
               for (int ch = 0; ch < nch && ok; ++ch) {
-                const int slot = ai & 1;
-                if (ai >= 2 && !mbar_wait(&a_empty[slot], ((ai >> 1) - 1) & 1)) { ok = false; break; }
+                const int slot = ai % A_BUFS;
+                if (ai >= A_BUFS && !mbar_wait(&a_empty[slot], ((ai / A_BUFS) - 1) & 1)) { ok = false; break; }
                 mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
 #pragma unroll
                 for (int q = 0; q < CHUNK_KB; ++q)
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // let the copies already issued land before the CTA can leave
         for (int j = (bi > B_STAGES ? bi - B_STAGES : 0); j < bi; ++j)
           mbar_wait(&b_full[j % B_STAGES], (j / B_STAGES) & 1);
-        for (int j = (ai > 2 ? ai - 2 : 0); j < ai; ++j) mbar_wait(&a_full[j & 1], (j >> 1) & 1);
+        for (int j = (ai > A_BUFS ? ai - A_BUFS : 0); j < ai; ++j) mbar_wait(&a_full[j % A_BUFS], (j / A_BUFS) & 1);
       }
     }
   } else if (warp == 1) {
@@ -410,8 +412,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int thi = hi - s < Su ? hi - s : Su;
               if (tlo > thi) continue;
               for (int ch = 0; ch < nch && ok; ++ch) {
-                const int aslot = ai & 1;
-                if (!mbar_wait(&a_full[aslot], (ai >> 1) & 1)) { ok = false; break; }
+                const int aslot = ai % A_BUFS;
+                if (!mbar_wait(&a_full[aslot], (ai / A_BUFS) & 1)) { ok = false; break; }
                 ++ai;
                 tc_fence_after();
                 const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
