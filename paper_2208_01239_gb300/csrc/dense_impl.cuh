@@ -43,14 +43,37 @@ constexpr int TK = 16;   // k step of the GEMM mainloop
 constexpr int NTH = 256; // threads per GEMM / TRSM CTA
 
 // ------------------------------------------------------------------ mainloop
-// acc[r][c] += sum_{k in [kbeg, kend)} opA(i0 + ty + 16 r, k) * opB(k, j0 + tx + 16 c)
+// acc[r][c] += sum_{k in [kbeg, kend)} opA(i0 + 4 ty + r, k) * opB(k, j0 + 4 tx + c)
 // where opA(i, k) = A[i][k] (OP_N), A[k][i] (OP_T) or conj(A[k][i]) (OP_C),
 // and opB(k, j) = B[k][j] (OP_N), B[j][k] (OP_T) or conj(B[j][k]) (OP_C).
 // Out-of-range rows (>= M), columns (>= N) and k (>= kend) read as zero.
+// Each thread owns 4 consecutive rows and columns, so that its operands come
+// from shared memory as 16-byte vectors (2 vector loads per 16 FMAs: the
+// FP32 path would otherwise be bound by shared-memory loads); rows are padded
+// to keep 16-byte alignment.
 template <typename T> struct SmemAB {
-  T a[TK][TB + 1];
-  T b[TK][TB + 1];
+  static constexpr int LD = TB + (16 / (int)sizeof(T) > 1 ? 16 / (int)sizeof(T) : 1);
+  T a[TK][LD];
+  T b[TK][LD];
 };
+
+// 4 consecutive elements from a 16-byte aligned shared-memory address
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void ld4(const zf* p, zf (&v)[4]) {
+  const float4 q0 = reinterpret_cast<const float4*>(p)[0], q1 = reinterpret_cast<const float4*>(p)[1];
+  v[0] = zf{q0.x, q0.y}; v[1] = zf{q0.z, q0.w}; v[2] = zf{q1.x, q1.y}; v[3] = zf{q1.z, q1.w};
+}
+__device__ __forceinline__ void ld4(const zd* p, zd (&v)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = p[i];
+}
 
 template <typename T, int OPA>
 __device__ __forceinline__ T load_opA(const T* A, int64_t lda, int i, int k, int M, int kend) {
@@ -109,10 +132,8 @@ __device__ __forceinline__ void mainloop(T (&acc)[4][4], SmemAB<T>& sm, const T*
 #pragma unroll 4
     for (int kk = 0; kk < TK; ++kk) {
       T av[4], bv[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = sm.a[kk][ty + 16 * r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = sm.b[kk][tx + 16 * c];
+      ld4(&sm.a[kk][4 * ty], av);
+      ld4(&sm.b[kk][4 * tx], bv);
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -192,7 +213,7 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+      int i = i0 + 4 * ty + r, j = j0 + 4 * tx + c;
       if (i < M && j < N) epi(b, i, j, acc[r][c]);
     }
 }
@@ -264,7 +285,7 @@ __global__ void __launch_bounds__(NTH) trsm_step_kernel(int n, int nrhs, int kb,
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      int rl = ty + 16 * r, cl = tx + 16 * c;
+      int rl = 4 * ty + r, cl = 4 * tx + c;
       int gr = r0 + rl, gc = c0 + cl;
       T bv = zero_v<T>();
       if (gr < n && gc < nrhs) {
