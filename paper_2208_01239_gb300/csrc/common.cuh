@@ -47,6 +47,16 @@ template <> __host__ __device__ __forceinline__ zf one_v<zf>() { return zf{1.0f,
 template <typename T> __host__ __device__ __forceinline__ T zero_v() { return zero_of(T{}); }
 
 // acc += a * b
+// warp shuffle of a scalar or an interleaved complex number
+__device__ __forceinline__ double shfl_(unsigned m, double v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ float shfl_(unsigned m, float v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ zd shfl_(unsigned m, zd v, int src) {
+  return zd{__shfl_sync(m, v.x, src), __shfl_sync(m, v.y, src)};
+}
+__device__ __forceinline__ zf shfl_(unsigned m, zf v, int src) {
+  return zf{__shfl_sync(m, v.x, src), __shfl_sync(m, v.y, src)};
+}
+
 __device__ __forceinline__ void mac(double& acc, double a, double b) { acc = fma(a, b, acc); }
 __device__ __forceinline__ void mac(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
 __device__ __forceinline__ void mac(zd& acc, zd a, zd b) {

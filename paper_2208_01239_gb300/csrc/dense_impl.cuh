@@ -317,31 +317,36 @@ __global__ void __launch_bounds__(NTH) trsm_step_kernel(int n, int nrhs, int kb,
   __syncthreads();
   if (t < TB) sm.dinv[t] = UNIT ? one_v<T>() : recip_(sm.u.d[t][t]);
   __syncthreads();
-  // substitution: 4 lanes per column (same warp), 64 columns
+  // substitution, column-oriented: the 4 lanes of a column (consecutive lanes
+  // of one warp) hold its rows l = part + 4 i in registers; step rr finishes
+  // x_rr (its owner lane scales by 1 / d_rr), passes it to the other three by
+  // a shuffle, and every lane removes d[l][rr] x_rr from its unfinished rows
+  // with independent FMAs.
   {
     const int col = t >> 2, part = t & 3;
     const unsigned mask = 0xffffffffu;
+    const int src = (threadIdx.x & 31) & ~3;
+    T wr[TB / 4];
+#pragma unroll
+    for (int i = 0; i < TB / 4; ++i) wr[i] = sm.w[part + 4 * i][col];
+#pragma unroll
     for (int s = 0; s < TB; ++s) {
-      int rr = LOWER ? s : (TB - 1 - s);
-      T p = zero_v<T>();
-      if (LOWER) {
-        for (int l = part; l < rr; l += 4) mac(p, sm.u.d[rr][l], sm.w[l][col]);
-      } else {
-        for (int l = rr + 1 + part; l < TB; l += 4) mac(p, sm.u.d[rr][l], sm.w[l][col]);
+      const int rr = LOWER ? s : (TB - 1 - s);
+      T x = zero_v<T>();
+      if (part == (rr & 3)) {
+        wr[rr >> 2] = mul_(wr[rr >> 2], sm.dinv[rr]);
+        x = wr[rr >> 2];
       }
-      // reduce over the 4 lanes of this column
-      if constexpr (is_cplx<T>::value) {
-        p.x += __shfl_xor_sync(mask, p.x, 1);
-        p.y += __shfl_xor_sync(mask, p.y, 1);
-        p.x += __shfl_xor_sync(mask, p.x, 2);
-        p.y += __shfl_xor_sync(mask, p.y, 2);
-      } else {
-        p += __shfl_xor_sync(mask, p, 1);
-        p += __shfl_xor_sync(mask, p, 2);
+      x = shfl_(mask, x, src | (rr & 3));
+      const T nx = neg_(x);
+#pragma unroll
+      for (int i = 0; i < TB / 4; ++i) {
+        const int l = part + 4 * i;
+        if (LOWER ? (l > rr) : (l < rr)) mac(wr[i], sm.u.d[l][rr], nx);
       }
-      if (part == 0) sm.w[rr][col] = mul_(sub_(sm.w[rr][col], p), sm.dinv[rr]);
-      __syncwarp();
     }
+#pragma unroll
+    for (int i = 0; i < TB / 4; ++i) sm.w[part + 4 * i][col] = wr[i];
   }
   __syncthreads();
   for (int e = t; e < TB * TB; e += NTH) {
