@@ -194,7 +194,9 @@ template <typename R> struct EpiFrobOut {
 };
 
 // tile_mode: 0 = all tiles; 1 = only tiles that touch the lower triangle
-// (j0 <= i0 + 63), for products known to be symmetric / Hermitian.
+// (j0 <= i0 + 63), for products known to be symmetric / Hermitian; 2 = the
+// sum starts at k = max(i0, j0), for op(A) op(B) = L^T L or L^H L with L lower
+// triangular (opA(i, k) = 0 for k < i, opB(k, j) = 0 for k < j).
 template <typename T, int OPA, int OPB, class Epi>
 __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<const T> A, MatB<const T> B, Epi epi,
                                                    int tile_mode) {
@@ -207,7 +209,8 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = zero_v<T>();
-  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, 0, K);
+  const int kbeg = tile_mode == 2 ? (i0 > j0 ? i0 : j0) : 0;
+  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, kbeg, K);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int r = 0; r < 4; ++r)

@@ -338,9 +338,12 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
   trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X2 = L1^{-T} X1
   potrf<R>(n, batch, p.S, info, n, st);                                                  // S = R2^T R2
   trsm<R, OP_N, true, false, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // X5 = L2^{-1}
-  trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);  // X6 = L2^{-T} X5
-  EpiFrobOut<R> epi{X, cst(p.Y), nullptr, n, nullptr};
-  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.Y), epi, 0, st);           // X = X6 - i X2 X6
+  // X6 = L2^{-T} X5 = X5^T X5 (S^{-1} = L2^{-T} L2^{-1}): a product of the
+  // triangular inverse with itself, summed over k >= max(i, j), into the
+  // plane of S (its factor is no longer needed)
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<R>(p.S, (R)1, (R)0, true), 2, st);
+  EpiFrobOut<R> epi{X, cst(p.S), nullptr, n, nullptr};
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.S), epi, 0, st);           // X = X6 - i X2 X6
 }
 
 // Complex LU inversion (Algorithm "Inversion with LU decomposition").
@@ -388,7 +391,9 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
   potrf<C>(n, batch, p.W, info, 0, st);                                                  // M = R^H R, L = R^H
   trsm<C, OP_N, true, false, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);    // X1 = L^{-1}
-  trsm<C, OP_C, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), X, nullptr, st);    // X2 = L^{-H} X1
+  // X2 = L^{-H} X1 = X1^H X1: the triangular inverse times itself, summed
+  // over k >= max(i, j)
+  gemm_launch<C, OP_C, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<C>(X, one_v<C>(), zero_v<C>(), true), 2, st);
 }
 
 // ------------------------------------------------------------------ linear solve
