@@ -196,20 +196,20 @@ template <typename R> struct EpiFrobOut {
 // tile_mode: 0 = all tiles; 1 = only tiles that touch the lower triangle
 // (j0 <= i0 + 63), for products known to be symmetric / Hermitian; 2 = the
 // sum starts at k = max(i0, j0), for op(A) op(B) = L^T L or L^H L with L lower
-// triangular (opA(i, k) = 0 for k < i, opB(k, j) = 0 for k < j).
+// triangular (opA(i, k) = 0 for k < i, opB(k, j) = 0 for k < j); 3 = both.
 template <typename T, int OPA, int OPB, class Epi>
 __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<const T> A, MatB<const T> B, Epi epi,
                                                    int tile_mode) {
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * TB, j0 = blockIdx.x * TB;
-  if (tile_mode == 1 && j0 > i0 + TB - 1) return;
+  if ((tile_mode & 1) && j0 > i0 + TB - 1) return;
   __shared__ SmemAB<T> sm;
   T acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = zero_v<T>();
-  const int kbeg = tile_mode == 2 ? (i0 > j0 ? i0 : j0) : 0;
+  const int kbeg = (tile_mode & 2) ? (i0 > j0 ? i0 : j0) : 0;
   mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, kbeg, K);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -219,6 +219,31 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
       int i = i0 + 4 * ty + r, j = j0 + 4 * tx + c;
       if (i < M && j < N) epi(b, i, j, acc[r][c]);
     }
+}
+
+// ------------------------------------------------------------------ mirror
+// Completes a symmetric (CONJ = false) or Hermitian (CONJ = true) matrix whose
+// 64 x 64 tiles on and below the diagonal are computed: A[i][j] = op(A[j][i])
+// for every (i, j) whose 64-tile column is right of its 64-tile row, through
+// a 32 x 32 shared-memory transpose (grid: 32-tiles x 32-tiles x batch, 32 x 8
+// threads).
+template <typename T, bool CONJ>
+__global__ void __launch_bounds__(256) mirror_kernel(int n, MatB<T> A) {
+  __shared__ T tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  if ((j0 >> 6) <= (i0 >> 6)) return;  // on or below the diagonal tiles: computed
+  T* a = A.at(blockIdx.z);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // source rows j0.., columns i0.. (coalesced along i)
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, i = i0 + tx;
+    if (j < n && i < n) tile[r][tx] = a[(int64_t)j * A.ld + i];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, j = j0 + tx;
+    if (i < n && j < n) a[(int64_t)i * A.ld + j] = CONJ ? conj_(tile[tx][r]) : tile[tx][r];
+  }
 }
 
 // ------------------------------------------------------------------ TRSM step

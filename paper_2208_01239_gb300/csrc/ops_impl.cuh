@@ -148,6 +148,12 @@ inline EpiAxpby<T> axpby(MatB<T> D, T alpha, T beta, bool beta_zero) {
   return EpiAxpby<T>{D, MatB<const T>{D.p, D.ld, D.bs}, alpha, beta, beta_zero ? 1 : 0};
 }
 
+template <typename T, bool CONJ>
+inline void mirror(int n, int batch, MatB<T> A, cudaStream_t st) {
+  const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)batch);
+  FROB_LAUNCH(CONJ ? "mirror<herm>" : "mirror<sym>", st, mirror_kernel<T, CONJ><<<g, 256, 0, st>>>(n, A));
+}
+
 template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
 inline void trsm_smem_attr() {
   static bool done = false;
@@ -340,10 +346,17 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
   trsm<R, OP_N, true, false, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // X5 = L2^{-1}
   // X6 = L2^{-T} X5 = X5^T X5 (S^{-1} = L2^{-T} L2^{-1}): a product of the
   // triangular inverse with itself, summed over k >= max(i, j), into the
-  // plane of S (its factor is no longer needed)
-  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<R>(p.S, (R)1, (R)0, true), 2, st);
+  // plane of S (its factor is no longer needed); the product of a matrix
+  // with its own transpose is symmetric in floating point too, so the tiles on
+  // and below the diagonal are computed and the rest mirrored
+  gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<R>(p.S, (R)1, (R)0, true), 3, st);
+  mirror<R, false>(n, batch, p.S, st);
+  // X = X6 - i X2 X6, all tiles: X2 X6 is antisymmetric only up to rounding,
+  // and the two computed halves carry the correlated errors that keep the
+  // residual at the FP64 level; completing one half from the other raises it
+  // to about kappa u
   EpiFrobOut<R> epi{X, cst(p.S), nullptr, n, nullptr};
-  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.S), epi, 0, st);           // X = X6 - i X2 X6
+  gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.S), epi, 0, st);
 }
 
 // Complex LU inversion (Algorithm "Inversion with LU decomposition").
@@ -392,8 +405,11 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   potrf<C>(n, batch, p.W, info, 0, st);                                                  // M = R^H R, L = R^H
   trsm<C, OP_N, true, false, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);    // X1 = L^{-1}
   // X2 = L^{-H} X1 = X1^H X1: the triangular inverse times itself, summed
-  // over k >= max(i, j)
-  gemm_launch<C, OP_C, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<C>(X, one_v<C>(), zero_v<C>(), true), 2, st);
+  // over k >= max(i, j); Hermitian in floating point too (a matrix times its
+  // own conjugate transpose), so the tiles on and below the diagonal are
+  // computed and the rest mirrored
+  gemm_launch<C, OP_C, OP_N>(n, n, n, batch, cst(p.Y), cst(p.Y), axpby<C>(X, one_v<C>(), zero_v<C>(), true), 3, st);
+  mirror<C, true>(n, batch, X, st);
 }
 
 // ------------------------------------------------------------------ linear solve

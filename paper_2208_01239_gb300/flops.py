@@ -10,9 +10,11 @@ Two conventions are kept apart:
   identity right-hand side.
 * ``executed_*`` -- the work the CUDA path actually performs, stage by stage
   (zero blocks of triangular right-hand sides are skipped, the symmetric
-  product X1^T X1 forms the lower triangle only, and the inverse of a
-  Cholesky factor's Gram matrix, L^{-T} L^{-1}, is the product of the
-  triangular inverse with itself over k >= max(i, j), as LAPACK's potri).
+  product X1^T X1 forms the lower triangle only, the inverse of a Cholesky
+  factor's Gram matrix, L^{-T} L^{-1}, is the product of the triangular
+  inverse with itself over k >= max(i, j), as LAPACK's potri, forming the
+  tiles on and below the diagonal only, since such a product is symmetric /
+  Hermitian in floating point too).
 
 ``nominal`` = 8 n^3 is the same for every method, so that TFLOP/s figures are
 comparable the way inversions/s are.
@@ -36,8 +38,8 @@ EXECUTED_STAGES = {
     "cplx_lu": [("zgetrf", 4 * F(2, 3)), ("z U^{-1} L^{-1} P", 4 * F(4, 3))],
     "frob_chol": [("potrf A", F(1, 3)), ("R1^T X1 = B", F(1)), ("S = A - X1^T X1 (lower)", F(1)),
                   ("R1 X2 = X1", F(1)), ("potrf S", F(1, 3)), ("R2^T X5 = I", F(1, 3)),
-                  ("X6 = X5^T X5", F(2, 3)), ("X2 X6", F(2))],
-    "cplx_chol": [("zpotrf", 4 * F(1, 3)), ("R^H X1 = I", 4 * F(1, 3)), ("X2 = X1^H X1", 4 * F(2, 3))],
+                  ("X6 = X5^T X5 (lower)", F(1, 3)), ("X2 X6", F(2))],
+    "cplx_chol": [("zpotrf", 4 * F(1, 3)), ("R^H X1 = I", 4 * F(1, 3)), ("X2 = X1^H X1 (lower)", 4 * F(1, 3))],
 }
 EXECUTED = {k: sum(c for _, c in v) for k, v in EXECUTED_STAGES.items()}
 

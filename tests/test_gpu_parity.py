@@ -186,7 +186,11 @@ def test_config2_hpd_batch64_n512(F):
         kappa = lams[b].max() / lams[b].min()
         for got in (x[b], xc[b]):
             assert metrics.forward_error(got, exact) <= 32 * 512 * kappa * U["fp64"]
-            assert metrics.residual_fro(ms[b], got) <= 1e-13
+            # both routes reach the FP64 level here (~5e-17); 1e-15 would
+            # catch a kappa u residual (~1e-14 at kappa 1e4), e.g. from
+            # completing a half of X2 X6 that is antisymmetric only up to
+            # rounding
+            assert metrics.residual_fro(ms[b], got) <= 1e-15
     for b in (0, 31, 63):
         ref = oracle.cplx_chol_inv(ms[b])
         kappa = lams[b].max() / lams[b].min()

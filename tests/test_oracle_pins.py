@@ -277,8 +277,8 @@ def test_paper_flop_counts():
 def test_executed_flop_counts():
     assert flops.EXECUTED["frob_lu"] == flops.F(26, 3)
     assert flops.EXECUTED["cplx_lu"] == 8
-    assert flops.EXECUTED["frob_chol"] == flops.F(20, 3)
-    assert flops.EXECUTED["cplx_chol"] == flops.F(16, 3)
+    assert flops.EXECUTED["frob_chol"] == flops.F(19, 3)
+    assert flops.EXECUTED["cplx_chol"] == 4
     assert flops.nominal(10) == 8000.0
 
 
