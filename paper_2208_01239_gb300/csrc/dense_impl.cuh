@@ -196,7 +196,10 @@ template <typename R> struct EpiFrobOut {
 // tile_mode: 0 = all tiles; 1 = only tiles that touch the lower triangle
 // (j0 <= i0 + 63), for products known to be symmetric / Hermitian; 2 = the
 // sum starts at k = max(i0, j0), for op(A) op(B) = L^T L or L^H L with L lower
-// triangular (opA(i, k) = 0 for k < i, opB(k, j) = 0 for k < j); 3 = both.
+// triangular (opA(i, k) = 0 for k < i, opB(k, j) = 0 for k < j); 3 = both;
+// bit 4: the sum starts at k = j0 (opB lower triangular: opB(k, j) = 0 for
+// k < j); bit 8: it ends at k = i0 + 64 (opA lower triangular: opA(i, k) = 0
+// for k > i).
 template <typename T, int OPA, int OPB, class Epi>
 __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<const T> A, MatB<const T> B, Epi epi,
                                                    int tile_mode) {
@@ -209,8 +212,10 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = zero_v<T>();
-  const int kbeg = (tile_mode & 2) ? (i0 > j0 ? i0 : j0) : 0;
-  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, kbeg, K);
+  int kbeg = (tile_mode & 2) ? (i0 > j0 ? i0 : j0) : 0;
+  if ((tile_mode & 4) && j0 > kbeg) kbeg = j0;
+  const int kend = ((tile_mode & 8) && i0 + TB < K) ? i0 + TB : K;
+  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, kbeg, kend);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -266,6 +271,44 @@ template <typename T> struct SmemTrsm {
   T w[TB][TB + 1];
   T dinv[TB];
 };
+
+// Substitution with the 64 x 64 triangular block sm.u.d (its reciprocal
+// diagonal in sm.dinv) on the 64 right-hand sides in sm.w, in place,
+// column-oriented: the 4 lanes of a column (consecutive lanes of one warp)
+// hold its rows l = part + 4 i in registers; step rr finishes x_rr (its owner
+// lane scales by 1 / d_rr), passes it to the other three by a shuffle, and
+// every lane removes d[l][rr] x_rr from its unfinished rows with independent
+// FMAs.  Ends with a __syncthreads.
+template <typename T, bool LOWER>
+__device__ __forceinline__ void subst64(SmemTrsm<T>& sm, int t) {
+  {
+    const int col = t >> 2, part = t & 3;
+    const unsigned mask = 0xffffffffu;
+    const int src = (threadIdx.x & 31) & ~3;
+    T wr[TB / 4];
+#pragma unroll
+    for (int i = 0; i < TB / 4; ++i) wr[i] = sm.w[part + 4 * i][col];
+#pragma unroll
+    for (int s = 0; s < TB; ++s) {
+      const int rr = LOWER ? s : (TB - 1 - s);
+      T x = zero_v<T>();
+      if (part == (rr & 3)) {
+        wr[rr >> 2] = mul_(wr[rr >> 2], sm.dinv[rr]);
+        x = wr[rr >> 2];
+      }
+      x = shfl_(mask, x, src | (rr & 3));
+      const T nx = neg_(x);
+#pragma unroll
+      for (int i = 0; i < TB / 4; ++i) {
+        const int l = part + 4 * i;
+        if (LOWER ? (l > rr) : (l < rr)) mac(wr[i], sm.u.d[l][rr], nx);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TB / 4; ++i) sm.w[part + 4 * i][col] = wr[i];
+  }
+  __syncthreads();
+}
 
 template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
 __global__ void __launch_bounds__(NTH) trsm_step_kernel(int n, int nrhs, int kb, MatB<const T> Tm, MatB<const T> Bm,
@@ -345,42 +388,48 @@ __global__ void __launch_bounds__(NTH) trsm_step_kernel(int n, int nrhs, int kb,
   __syncthreads();
   if (t < TB) sm.dinv[t] = UNIT ? one_v<T>() : recip_(sm.u.d[t][t]);
   __syncthreads();
-  // substitution, column-oriented: the 4 lanes of a column (consecutive lanes
-  // of one warp) hold its rows l = part + 4 i in registers; step rr finishes
-  // x_rr (its owner lane scales by 1 / d_rr), passes it to the other three by
-  // a shuffle, and every lane removes d[l][rr] x_rr from its unfinished rows
-  // with independent FMAs.
-  {
-    const int col = t >> 2, part = t & 3;
-    const unsigned mask = 0xffffffffu;
-    const int src = (threadIdx.x & 31) & ~3;
-    T wr[TB / 4];
-#pragma unroll
-    for (int i = 0; i < TB / 4; ++i) wr[i] = sm.w[part + 4 * i][col];
-#pragma unroll
-    for (int s = 0; s < TB; ++s) {
-      const int rr = LOWER ? s : (TB - 1 - s);
-      T x = zero_v<T>();
-      if (part == (rr & 3)) {
-        wr[rr >> 2] = mul_(wr[rr >> 2], sm.dinv[rr]);
-        x = wr[rr >> 2];
-      }
-      x = shfl_(mask, x, src | (rr & 3));
-      const T nx = neg_(x);
-#pragma unroll
-      for (int i = 0; i < TB / 4; ++i) {
-        const int l = part + 4 * i;
-        if (LOWER ? (l > rr) : (l < rr)) mac(wr[i], sm.u.d[l][rr], nx);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < TB / 4; ++i) sm.w[part + 4 * i][col] = wr[i];
-  }
-  __syncthreads();
+  subst64<T, LOWER>(sm, t);
   for (int e = t; e < TB * TB; e += NTH) {
     int rl = e / TB, cl = e % TB;
     int gr = r0 + rl, gc = c0 + cl;
     if (gr < n && gc < nrhs) Xb[(int64_t)gr * X.ld + gc] = sm.w[rl][cl];
+  }
+}
+
+// Diagonal blocks of the inverse of a lower triangular L (unit diagonal if
+// UNIT): X[kb][kb] = L[kb][kb]^{-1} for block row kb = blockIdx.x, and the
+// tiles right of it in block row kb set to zero (grid: blocks x batch).
+template <typename T, bool UNIT>
+__global__ void __launch_bounds__(NTH) trtri_diag_kernel(int n, MatB<const T> Lm, MatB<T> X) {
+  const int b = blockIdx.z;
+  const int kb = blockIdx.x;
+  const int r0 = kb * TB;
+  const int t = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SmemTrsm<T>& sm = *reinterpret_cast<SmemTrsm<T>*>(smraw);
+  T* Xb = X.at(b);
+  const T* Lb = Lm.at(b);
+  for (int e = t; e < TB * TB; e += NTH) {
+    const int rl = e / TB, cl = e % TB;
+    const int gr = r0 + rl, gc = r0 + cl;
+    T v = zero_v<T>();
+    if (gr < n && gc < n && cl <= rl) v = Lb[(int64_t)gr * Lm.ld + gc];
+    if (rl == cl && (UNIT || gr >= n)) v = one_v<T>();
+    sm.u.d[rl][cl] = v;
+    sm.w[rl][cl] = rl == cl ? one_v<T>() : zero_v<T>();
+  }
+  __syncthreads();
+  if (t < TB) sm.dinv[t] = UNIT ? one_v<T>() : recip_(sm.u.d[t][t]);
+  __syncthreads();
+  subst64<T, true>(sm, t);
+  for (int e = t; e < TB * TB; e += NTH) {
+    const int rl = e / TB, cl = e % TB;
+    const int gr = r0 + rl, gc = r0 + cl;
+    if (gr < n && gc < n) Xb[(int64_t)gr * X.ld + gc] = sm.w[rl][cl];
+  }
+  for (int e = t; e < TB * (n - r0 - TB); e += NTH) {  // right of the diagonal block
+    const int rl = e / (n - r0 - TB), c = r0 + TB + e % (n - r0 - TB);
+    if (r0 + rl < n) Xb[(int64_t)(r0 + rl) * X.ld + c] = zero_v<T>();
   }
 }
 

@@ -181,6 +181,39 @@ inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm,
   }
 }
 
+// X = L^{-1} for lower triangular L (unit diagonal if UNIT), recursively:
+// the 64 x 64 diagonal blocks are inverted in one launch, then neighbouring
+// blocks of size s = 64, 128, ... are joined,
+//   [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}],
+// by two batched products per pair that skip the zero triangles (B A^{-1}
+// from k = j0, C^{-1} (B A^{-1}) up to k = i0 + 64).  Tmp: n x n scratch of
+// the same layout (its lower blocks are overwritten).
+template <typename T, bool UNIT>
+inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(trtri_diag_kernel<T, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SmemTrsm<T>));
+    attr = true;
+  }
+  static const std::string name = std::string("trtri_diag<") + type_tag<T>() + ">";
+  const int nblk = (n + TB - 1) / TB;
+  FROB_LAUNCH(name.c_str(), st,
+              trtri_diag_kernel<T, UNIT><<<dim3(nblk, 1, batch), NTH, sizeof(SmemTrsm<T>), st>>>(n, Lm, X));
+  auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
+  for (int s = TB; s < n; s *= 2) {
+    for (int r = 0; r + s < n; r += 2 * s) {
+      const int sc = (n - r - s) < s ? (n - r - s) : s;  // order of C (the last one may be short)
+      MatB<const T> B = Lm.sub(r + s, r);
+      MatB<T> Tp = Tmp.sub(r + s, r);
+      gemm_launch<T, OP_N, OP_N>(sc, s, s, batch, B, cst(X.sub(r, r)), axpby<T>(Tp, one_v<T>(), zero_v<T>(), true), 4,
+                                 st);                                                     // B A^{-1}
+      gemm_launch<T, OP_N, OP_N>(sc, s, sc, batch, cst(X.sub(r + s, r + s)), cst(Tp),
+                                 axpby<T>(X.sub(r + s, r), neg_(one_v<T>()), zero_v<T>(), true), 8, st);  // -C^{-1} (B A^{-1})
+    }
+  }
+}
+
 template <typename T> inline void panel_smem_attr() {
   static bool done = false;
   if (!done) {
@@ -311,7 +344,7 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
                              st);                                                       // S = A + B X1
   getrf<R>(n, batch, p.S, p.piv2, info, n, st);                                        // S = P2^T L2 U2
   rowperm(n, batch, p.piv2, p.rp2, st);
-  trsm<R, OP_N, true, true, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // Y = L2^{-1}
+  trtri<R, true>(n, batch, cst(p.S), p.Y, p.LA, st);                                     // Y = L2^{-1}
   trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
   EpiFrobOut<R> epi{X, cst(p.Y), p.rp2, n, o.almost_sure ? info : nullptr};
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.X1), cst(p.Y), epi, 0, st);          // X = Z P2 - i X1 Z P2
@@ -343,7 +376,7 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
                              st);                                                         // S = A - X1^T X1
   trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X2 = L1^{-T} X1
   potrf<R>(n, batch, p.S, info, n, st);                                                  // S = R2^T R2
-  trsm<R, OP_N, true, false, true>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st);    // X5 = L2^{-1}
+  trtri<R, false>(n, batch, cst(p.S), p.Y, p.LA, st);                                    // X5 = L2^{-1}
   // X6 = L2^{-T} X5 = X5^T X5 (S^{-1} = L2^{-T} L2^{-1}): a product of the
   // triangular inverse with itself, summed over k >= max(i, j), into the
   // plane of S (its factor is no longer needed); the product of a matrix
@@ -380,7 +413,7 @@ void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_in
   FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
   getrf<C>(n, batch, p.W, p.piv, info, 0, st);                                           // M = P^T L U
   rowperm(n, batch, p.piv, p.rp, st);
-  trsm<C, OP_N, true, true, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);     // Y = L^{-1}
+  trtri<C, true>(n, batch, cst(p.W), p.Y, X, st);                                         // Y = L^{-1}
   trsm<C, OP_N, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);  // Z = U^{-1} Y
   FROB_LAUNCH("colperm", st, colperm_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(p.Y), X, p.rp));          // X = Z P
 }
@@ -403,7 +436,7 @@ void cplx_chol_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_
   auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
   potrf<C>(n, batch, p.W, info, 0, st);                                                  // M = R^H R, L = R^H
-  trsm<C, OP_N, true, false, true>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);    // X1 = L^{-1}
+  trtri<C, false>(n, batch, cst(p.W), p.Y, X, st);                                        // X1 = L^{-1}
   // X2 = L^{-H} X1 = X1^H X1: the triangular inverse times itself, summed
   // over k >= max(i, j); Hermitian in floating point too (a matrix times its
   // own conjugate transpose), so the tiles on and below the diagonal are
