@@ -285,7 +285,9 @@ uint64_t frob_kernel_launches(void);
  * frob_profile_report() waits for the recorded events, writes a JSON object
  * {"<kernel variant>": [launches, total_ms], ...} into buf (truncated to len
  * bytes, NUL-terminated), releases the records and returns the length needed
- * including the NUL.  Not for use inside CUDA graph capture. */
+ * including the NUL.  Not for use inside CUDA graph capture.  While profiling
+ * is on, a call whose batch is split over internal streams runs the slices
+ * one after the other on the caller's stream (each kernel then runs alone). */
 void frob_profile_enable(int on);
 size_t frob_profile_report(char* buf, size_t len);
 

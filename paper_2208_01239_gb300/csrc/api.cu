@@ -121,6 +121,72 @@ frob_status launched() {
   return e == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;
 }
 
+// Batch slices on internal streams.  The blocked factorisations and solves
+// are sequences of launches of a few hundred CTAs each; running two halves of
+// the batch on two streams forked from the caller's stream (and joined back
+// before the call returns to it) lets one half's wave tails and short launches
+// overlap the other half's work.  The streams and events belong to the host
+// thread and device (created on first use); the fork / join pattern is also
+// valid inside a CUDA-graph capture of the caller's stream.
+constexpr int NSPLIT = 2;
+struct SplitStreams {
+  cudaStream_t s[NSPLIT];
+  cudaEvent_t fork, join[NSPLIT];
+};
+SplitStreams* split_streams() {
+  thread_local std::map<int, SplitStreams> sets;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = sets.find(dev);
+  if (it != sets.end()) return &it->second;
+  SplitStreams ss{};
+  for (int k = 0; k < NSPLIT; ++k) {
+    cudaStreamCreateWithFlags(&ss.s[k], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&ss.join[k], cudaEventDisableTiming);
+  }
+  cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+  return &(sets[dev] = ss);
+}
+// slice k of a batch: [first, first + count)
+inline int slice_first(int batch, int k) { return (int)(((int64_t)batch * k) / NSPLIT); }
+inline int slice_count(int batch, int k) { return slice_first(batch, k + 1) - slice_first(batch, k); }
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+// Workspace of a split call: one carve per slice.
+template <class WsOf> size_t split_ws(int batch, WsOf ws_of) {
+  if (batch < NSPLIT) return ws_of(batch);
+  size_t total = 0;
+  for (int k = 0; k < NSPLIT; ++k) total += round256(ws_of(slice_count(batch, k)));
+  return total;
+}
+// run(first, count, workspace, stream) per slice.  While per-kernel profiling
+// is on, the slices run one after the other on the caller's stream, so that
+// the events around a launch time that kernel alone.
+template <class WsOf, class Run> void split_run(int batch, void* ws, cudaStream_t st, WsOf ws_of, Run run) {
+  if (batch < NSPLIT) {
+    run(0, batch, ws, st);
+    return;
+  }
+  if (g_prof_on.load(std::memory_order_relaxed)) {
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    for (int k = 0; k < NSPLIT; ++k) {
+      run(slice_first(batch, k), slice_count(batch, k), w, st);
+      w += round256(ws_of(slice_count(batch, k)));
+    }
+    return;
+  }
+  SplitStreams* ss = split_streams();
+  cudaEventRecord(ss->fork, st);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  for (int k = 0; k < NSPLIT; ++k) {
+    const int first = slice_first(batch, k), count = slice_count(batch, k);
+    cudaStreamWaitEvent(ss->s[k], ss->fork, 0);
+    run(first, count, w, ss->s[k]);
+    w += round256(ws_of(count));
+    cudaEventRecord(ss->join[k], ss->s[k]);
+  }
+  for (int k = 0; k < NSPLIT; ++k) cudaStreamWaitEvent(st, ss->join[k], 0);
+}
+
 template <typename T> MatB<const T> in_view(const void* p, int64_t ld, int64_t s) {
   return MatB<const T>{static_cast<const T*>(p), ld, s};
 }
@@ -140,13 +206,21 @@ size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
   const bool f32 = prec == FROB_FP32;
   switch (op) {
     case FROB_OP_INV:
-      return f32 ? frob_lu_ws<float>(n, batch, nullptr, nullptr) : frob_lu_ws<double>(n, batch, nullptr, nullptr);
+      return split_ws(batch, [&](int b) {
+        return f32 ? frob_lu_ws<float>(n, b, nullptr, nullptr) : frob_lu_ws<double>(n, b, nullptr, nullptr);
+      });
     case FROB_OP_INV_HPD:
-      return f32 ? frob_chol_ws<float>(n, batch, nullptr, nullptr) : frob_chol_ws<double>(n, batch, nullptr, nullptr);
+      return split_ws(batch, [&](int b) {
+        return f32 ? frob_chol_ws<float>(n, b, nullptr, nullptr) : frob_chol_ws<double>(n, b, nullptr, nullptr);
+      });
     case FROB_OP_CPLX_LU:
-      return f32 ? cplx_lu_ws<zf>(n, batch, nullptr, nullptr) : cplx_lu_ws<zd>(n, batch, nullptr, nullptr);
+      return split_ws(batch, [&](int b) {
+        return f32 ? cplx_lu_ws<zf>(n, b, nullptr, nullptr) : cplx_lu_ws<zd>(n, b, nullptr, nullptr);
+      });
     case FROB_OP_CPLX_CHOL:
-      return f32 ? cplx_chol_ws<zf>(n, batch, nullptr, nullptr) : cplx_chol_ws<zd>(n, batch, nullptr, nullptr);
+      return split_ws(batch, [&](int b) {
+        return f32 ? cplx_chol_ws<zf>(n, b, nullptr, nullptr) : cplx_chol_ws<zd>(n, b, nullptr, nullptr);
+      });
     case FROB_OP_ADJOINT:
       return f32 ? adjoint_ws<float>(n, batch) : adjoint_ws<double>(n, batch);
     default:
@@ -168,10 +242,22 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
         mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, false);
     return ms != FROB_OK ? ms : launched();
   }
-  if (o.prec == FROB_FP32)
-    frob_lu_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), o, ws, info, st);
+  // (the almost-sure draw of mu depends on the matrix index: one slice)
+  const int sb = o.almost_sure ? 1 : batch;
+  auto run = [&](int first, int count, void* w, cudaStream_t s2) {
+    if (o.prec == FROB_FP32)
+      frob_lu_run<float>(n, count, in_view<zf>(M, ldm, sm).at_batch(first), out_view<zf>(X, ldx, sx).at_batch(first), o,
+                         w, info + first, s2);
+    else
+      frob_lu_run<double>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first),
+                          o, w, info + first, s2);
+  };
+  if (sb == 1)
+    run(0, batch, ws, st);
   else
-    frob_lu_run<double>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st);
+    split_run(batch, ws, st, [&](int b) {
+      return o.prec == FROB_FP32 ? frob_lu_ws<float>(n, b, nullptr, nullptr) : frob_lu_ws<double>(n, b, nullptr, nullptr);
+    }, run);
   return launched();
 }
 
@@ -189,10 +275,16 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
         mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, true);
     return ms != FROB_OK ? ms : launched();
   }
-  if (o.prec == FROB_FP32)
-    frob_chol_run<float>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
-  else
-    frob_chol_run<double>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  split_run(batch, ws, st, [&](int b) {
+    return o.prec == FROB_FP32 ? frob_chol_ws<float>(n, b, nullptr, nullptr) : frob_chol_ws<double>(n, b, nullptr, nullptr);
+  }, [&](int first, int count, void* w, cudaStream_t s2) {
+    if (o.prec == FROB_FP32)
+      frob_chol_run<float>(n, count, in_view<zf>(M, ldm, sm).at_batch(first), out_view<zf>(X, ldx, sx).at_batch(first),
+                           w, info + first, s2);
+    else
+      frob_chol_run<double>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first),
+                            w, info + first, s2);
+  });
   return launched();
 }
 
@@ -203,10 +295,16 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
                                frob_workspace_bytes(FROB_OP_CPLX_LU, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (prec == FROB_FP32)
-    cplx_lu_run<zf>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
-  else
-    cplx_lu_run<zd>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  split_run(batch, ws, st, [&](int b) {
+    return prec == FROB_FP32 ? cplx_lu_ws<zf>(n, b, nullptr, nullptr) : cplx_lu_ws<zd>(n, b, nullptr, nullptr);
+  }, [&](int first, int count, void* w, cudaStream_t s2) {
+    if (prec == FROB_FP32)
+      cplx_lu_run<zf>(n, count, in_view<zf>(M, ldm, sm).at_batch(first), out_view<zf>(X, ldx, sx).at_batch(first), w,
+                      info + first, s2);
+    else
+      cplx_lu_run<zd>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first), w,
+                      info + first, s2);
+  });
   return launched();
 }
 
@@ -217,10 +315,16 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
                                frob_workspace_bytes(FROB_OP_CPLX_CHOL, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (prec == FROB_FP32)
-    cplx_chol_run<zf>(n, batch, in_view<zf>(M, ldm, sm), out_view<zf>(X, ldx, sx), ws, info, st);
-  else
-    cplx_chol_run<zd>(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), ws, info, st);
+  split_run(batch, ws, st, [&](int b) {
+    return prec == FROB_FP32 ? cplx_chol_ws<zf>(n, b, nullptr, nullptr) : cplx_chol_ws<zd>(n, b, nullptr, nullptr);
+  }, [&](int first, int count, void* w, cudaStream_t s2) {
+    if (prec == FROB_FP32)
+      cplx_chol_run<zf>(n, count, in_view<zf>(M, ldm, sm).at_batch(first), out_view<zf>(X, ldx, sx).at_batch(first), w,
+                        info + first, s2);
+    else
+      cplx_chol_run<zd>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first), w,
+                        info + first, s2);
+  });
   return launched();
 }
 

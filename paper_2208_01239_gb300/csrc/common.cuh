@@ -143,6 +143,8 @@ template <typename T> struct MatB {
   int64_t bs;
   __host__ __device__ __forceinline__ T* at(int b) const { return p + (int64_t)b * bs; }
   __host__ __device__ __forceinline__ MatB sub(int64_t i, int64_t j) const { return MatB{p + i * ld + j, ld, bs}; }
+  // the batch starting at matrix `first`
+  __host__ __device__ __forceinline__ MatB at_batch(int64_t first) const { return MatB{p + first * bs, ld, bs}; }
 };
 
 template <typename T> __host__ __device__ inline MatB<T> matb(T* p, int64_t ld, int64_t bs) { return MatB<T>{p, ld, bs}; }
