@@ -201,7 +201,9 @@ extern "C" {
 size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
   if (n < 1 || batch < 1) return 0;
   if (mixed_prec(prec))
-    return ((op == FROB_OP_INV || op == FROB_OP_INV_HPD) && n <= 512) ? mixed::mixed_ws(n, batch) : 0;
+    return ((op == FROB_OP_INV || op == FROB_OP_INV_HPD) && n <= 512)
+               ? split_ws(batch, [&](int b) { return mixed::mixed_ws(n, b); })
+               : 0;
   if (!valid_prec(prec)) return 0;
   const bool f32 = prec == FROB_FP32;
   switch (op) {
@@ -238,8 +240,15 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mixed_prec(o.prec)) {
     if (o.almost_sure) return FROB_ERR_UNSUPPORTED;
-    frob_status ms =
-        mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, false);
+    if (n > 512) return FROB_ERR_UNSUPPORTED;
+    frob_status ms = FROB_OK;
+    split_run(batch, ws, st, [&](int b) { return mixed::mixed_ws(n, b); },
+              [&](int first, int count, void* w, cudaStream_t s2) {
+                frob_status r = mixed::mixed_run(n, count, in_view<zd>(M, ldm, sm).at_batch(first),
+                                                 out_view<zd>(X, ldx, sx).at_batch(first), o, w, info + first, s2,
+                                                 false);
+                if (r != FROB_OK) ms = r;
+              });
     return ms != FROB_OK ? ms : launched();
   }
   // (the almost-sure draw of mu depends on the matrix index: one slice)
@@ -271,8 +280,14 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mixed_prec(o.prec)) {
     if (n > 512) return FROB_ERR_UNSUPPORTED;
-    frob_status ms =
-        mixed::mixed_run(n, batch, in_view<zd>(M, ldm, sm), out_view<zd>(X, ldx, sx), o, ws, info, st, true);
+    frob_status ms = FROB_OK;
+    split_run(batch, ws, st, [&](int b) { return mixed::mixed_ws(n, b); },
+              [&](int first, int count, void* w, cudaStream_t s2) {
+                frob_status r = mixed::mixed_run(n, count, in_view<zd>(M, ldm, sm).at_batch(first),
+                                                 out_view<zd>(X, ldx, sx).at_batch(first), o, w, info + first, s2,
+                                                 true);
+                if (r != FROB_OK) ms = r;
+              });
     return ms != FROB_OK ? ms : launched();
   }
   split_run(batch, ws, st, [&](int b) {
