@@ -251,9 +251,18 @@ void launch_split(int n, int Kp, int batch, int S, const double* src, __nv_bfloa
   const int64_t warps = (int64_t)batch * n;  // one warp per (real, imaginary) row pair
   const int threads = 256;
   const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
-  FROB_LAUNCH("oz_split", st,
-              oz::oz_split_rows_kernel<<<blocks, threads, 0, st>>>(n, n, Kp, batch, S, src, n, (int64_t)n * n,
-                                                                   (int64_t)batch * n * n, dst, exps, skip));
+  const int64_t nn = (int64_t)n * n, ps = (int64_t)batch * n * n;
+#define FROB_SPLIT_S(SV)                                                                                        \
+  FROB_LAUNCH("oz_split", st,                                                                                  \
+              oz::oz_split_rows_kernel<SV><<<blocks, threads, 0, st>>>(n, n, Kp, batch, src, n, nn, ps, dst, exps, \
+                                                                         skip))
+  switch (S) {  // the digit counts this driver uses
+    case S_CORR: FROB_SPLIT_S(S_CORR); break;
+    case S_RESID: FROB_SPLIT_S(S_RESID); break;
+    case S_RESID_FINE: FROB_SPLIT_S(S_RESID_FINE); break;
+    default: break;
+  }
+#undef FROB_SPLIT_S
 }
 
 struct Layout {

@@ -132,10 +132,12 @@ __device__ __forceinline__ uint32_t bf16_bits_of_int(int d) {
 
 // One warp per row pair (real and imaginary).  Each lane keeps its 16
 // entries of each row (4 consecutive columns in each 128-wide block) in
-// registers between the maximum and the digit passes.
-__global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Kp, int batch, int S,
-                                                            const double* src, int64_t ld, int64_t bs, int64_t ps,
-                                                            __nv_bfloat16* dst, int* exps, const int* skip) {
+// registers between the maximum and the digit passes.  S is a template
+// parameter so that every digit shift is a constant.
+template <int S>
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Kp, int batch, const double* src,
+                                                            int64_t ld, int64_t bs, int64_t ps, __nv_bfloat16* dst,
+                                                            int* exps, const int* skip) {
   constexpr int NP = 2;
   constexpr int NJ = K_MAX / 128;
   const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int
 #pragma unroll
     for (int p = 0; p < NP; ++p) exps[((int64_t)(part0 + p) * batch + b) * rows + row] = e;
   long long off = 0;  // 64 (1 + 128 + ... + 128^(S-2))
+#pragma unroll
   for (int j = 0; j < S - 1; ++j) off = (off << 7) + 64;
   const int64_t plane = (int64_t)batch * rows * Kp;  // one digit slice
 #pragma unroll
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int
       long long G[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) G[q] = scaled_fixed(v[p][j][q], 7 * S - e) + off;
+#pragma unroll
       for (int sl = 0; sl < S; ++sl) {  // slice sl holds the digit of weight 2^(-7 (sl + 1))
         const int sh = 7 * (S - 1 - sl);
         uint32_t bits[4];
