@@ -25,9 +25,14 @@
 //                      search by warp-shuffle argmax.
 //   laswp_trsm_kernel  applies a panel's row swaps to the other columns and
 //                      forms U12 = L11^{-1} A12.
-//   potrf_diag_kernel  Cholesky of a panel's diagonal block (lower,
-//                      A = L L^H), one warp per matrix.
-//   potrf_rows_kernel  the rows below it, L21 = A21 L11^{-H}, one thread per row.
+//   trtri_diag_kernel  inverses of the 64x64 diagonal blocks of a lower
+//                      triangular matrix (the first step of trtri).
+//   potrf_panel_kernel one 32-wide panel of a blocked Cholesky (lower,
+//                      A = L L^H): the diagonal block by one warp in
+//                      registers (redone by every CTA), then the rows below
+//                      it, L21 = A21 L11^{-H}, one thread per row.
+//   mirror_kernel      completes a symmetric / Hermitian matrix from its
+//                      lower tiles.
 #pragma once
 
 #include <cstdint>
@@ -603,24 +608,19 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
   }
 }
 
-// Cholesky of the kb x kb diagonal block of the panel [k0, k0+kb) (lower,
-// A11 = L11 L11^H), one warp per matrix (grid: batch).  Lane r keeps row r of
-// the block in registers; step j broadcasts column j through shared memory
-// and every lane applies its rank-1 update with independent FMAs.  A
-// non-positive or non-finite diagonal reports FROB_ERR_NOT_HPD with
-// bad_index = k + 1 + info_off and continues with a unit pivot.
+// Cholesky of the kb x kb diagonal block at g (lower, A11 = L11 L11^H) by one
+// warp: lane r keeps row r in registers; step j broadcasts column j through
+// colj (shared memory) and every lane applies its rank-1 update with
+// independent FMAs.  Lane r returns row r of L11 in r[] (zeros above the
+// diagonal); the first non-positive or non-finite pivot is returned in *fail
+// (-1 if none; that pivot is replaced by 1).
 template <typename T>
-__global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int k0, int kb, MatB<T> A, frob_info* info,
-                                                         int info_off) {
+__device__ __forceinline__ void chol32_warp(const T* g, int64_t ld, int kb, T* colj, T (&r)[PANEL_MAX], int* fail) {
   using K = typename real_of<T>::type;
-  const int b = blockIdx.x;
-  const int lane = threadIdx.x;
-  __shared__ T colj[PANEL_MAX];
-  T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
-  T r[PANEL_MAX];
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < PANEL_MAX; ++c) r[c] = (lane < kb && c <= lane) ? g[(int64_t)lane * A.ld + c] : zero_v<T>();
-  int fail = -1;
+  for (int c = 0; c < PANEL_MAX; ++c) r[c] = (lane < kb && c <= lane) ? g[(int64_t)lane * ld + c] : zero_v<T>();
+  int f = -1;
 #pragma unroll
   for (int j = 0; j < PANEL_MAX; ++j) {
     if (j < kb) {
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int k0, int kb, M
       __syncwarp();
       const K d = real_(colj[j]);
       const bool ok = d > (K)0 && d < (K)INFINITY;
-      if (!ok && fail < 0) fail = j;
+      if (!ok && f < 0) f = j;
       const K l = ok ? sqrt(d) : (K)1;
       __syncwarp();
       if (lane == j) r[j] = from_real<T>(l);
@@ -642,28 +642,41 @@ __global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int k0, int kb, M
       __syncwarp();
     }
   }
-  if (fail >= 0 && lane == 0) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + fail + 1);
-  if (lane < kb)
-#pragma unroll
-    for (int c = 0; c < PANEL_MAX; ++c)
-      if (c <= lane) g[(int64_t)lane * A.ld + c] = r[c];
+  *fail = f;
 }
 
-// Rows below the diagonal block: L21 = A21 L11^{-H}, i.e. each row x solves
-// x L11^H = a (grid: row blocks of 128 x batch, one thread per row).
+// One step of the blocked Cholesky: the panel [k0, k0 + kb).  Every CTA
+// factors the diagonal block itself (warp 0, in registers; CTA 0 writes it
+// back and reports a non-positive or non-finite pivot as FROB_ERR_NOT_HPD with
+// bad_index = k + 1 + info_off, continuing with a unit pivot), then solves
+// its rows below it, L21 = A21 L11^{-H}, one thread per row: x L11^H = a.
+// Grid: row blocks of 128 (at least one) x batch.
 template <typename T>
-__global__ void __launch_bounds__(128) potrf_rows_kernel(int n, int k0, int kb, MatB<T> A) {
+__global__ void __launch_bounds__(128) potrf_panel_kernel(int n, int k0, int kb, MatB<T> A, frob_info* info,
+                                                          int info_off) {
   using K = typename real_of<T>::type;
   const int b = blockIdx.y;
   __shared__ T L[PANEL_MAX][PANEL_MAX + 1];
   __shared__ K dinv[PANEL_MAX];
+  __shared__ T colj[PANEL_MAX];
   T* Ab = A.at(b);
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int r = e / kb, c = e % kb;
-    L[r][c] = (c <= r) ? Ab[(int64_t)(k0 + r) * A.ld + k0 + c] : zero_v<T>();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    T r[PANEL_MAX];
+    int fail;
+    T* g = Ab + (int64_t)k0 * A.ld + k0;
+    chol32_warp<T>(g, A.ld, kb, colj, r, &fail);
+#pragma unroll
+    for (int c = 0; c < PANEL_MAX; ++c) L[lane][c] = r[c];
+    if (lane < kb) dinv[lane] = (K)1 / real_(r[lane]);
+    if (blockIdx.x == 0) {
+      if (fail >= 0 && lane == 0) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + fail + 1);
+      if (lane < kb)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c)
+          if (c <= lane) g[(int64_t)lane * A.ld + c] = r[c];
+    }
   }
-  __syncthreads();
-  if (threadIdx.x < kb) dinv[threadIdx.x] = (K)1 / real_(L[threadIdx.x][threadIdx.x]);
   __syncthreads();
   const int row = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;

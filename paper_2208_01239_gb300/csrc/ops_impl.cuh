@@ -256,15 +256,11 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
 }
 
 // Blocked right-looking Cholesky (A = L L^H, lower triangle, in place): per
-// 32-wide panel, the diagonal block by one warp per matrix, the rows below it
-// by one thread per row across the grid, then the trailing update of the
-// lower tiles.
-template <typename T> inline const char* potrf_diag_name() {
-  static const std::string s = std::string("potrf_diag<") + type_tag<T>() + ">";
-  return s.c_str();
-}
-template <typename T> inline const char* potrf_rows_name() {
-  static const std::string s = std::string("potrf_rows<") + type_tag<T>() + ">";
+// 32-wide panel, one launch for the diagonal block and the rows below it (the
+// block factored by one warp of every CTA, the rows one thread each), then
+// the trailing update of the lower tiles.
+template <typename T> inline const char* potrf_panel_name() {
+  static const std::string s = std::string("potrf_panel<") + type_tag<T>() + ">";
   return s.c_str();
 }
 
@@ -273,11 +269,11 @@ inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cu
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
-    FROB_LAUNCH(potrf_diag_name<T>(), st, potrf_diag_kernel<T><<<batch, 32, 0, st>>>(n, k0, kb, A, info, info_off));
     const int r = k0 + kb;
+    const int rb = r < n ? (n - r + 127) / 128 : 1;
+    FROB_LAUNCH(potrf_panel_name<T>(), st,
+                potrf_panel_kernel<T><<<dim3(rb, batch), 128, 0, st>>>(n, k0, kb, A, info, info_off));
     if (r < n) {
-      FROB_LAUNCH(potrf_rows_name<T>(), st,
-                  potrf_rows_kernel<T><<<dim3((n - r + 127) / 128, batch), 128, 0, st>>>(n, k0, kb, A));
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
       MatB<T> A22 = A.sub(r, r);
       gemm_launch<T, OP_N, OP_C>(n - r, n - r, kb, batch, L21, L21, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
