@@ -553,6 +553,94 @@ __global__ void __launch_bounds__(PANEL_THREADS) getrf_panel_kernel(int n, int k
 // inside the panel are skipped.
 constexpr int PANEL_MAX = 32;  // widest column panel of the blocked LU / Cholesky
 
+// As getrf_panel_kernel for panels of at most PANEL_THREADS rows (n - k0 <=
+// 512) and scalars of at most 8 bytes: thread r keeps row r of the panel in
+// registers; the pivot search reads column j from registers, the two rows of
+// a swap pass through shared memory, and the rank-1 update of the panel is
+// independent FMAs with the pivot row broadcast from shared memory.
+// Same results and reports as getrf_panel_kernel.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS) getrf_panel_reg_kernel(int n, int k0, int kb, MatB<T> A, int* piv,
+                                                                         frob_info* info, int info_off) {
+  using K = typename real_of<T>::type;
+  const int b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int m = n - k0;
+  __shared__ KeyIdx<K> red[PANEL_THREADS / 32];
+  __shared__ T prow[PANEL_MAX];
+  __shared__ T jrow[PANEL_MAX];
+  __shared__ int s_p;
+  __shared__ T s_rinv;
+  __shared__ int s_ok;
+  T* g = A.at(b) + (int64_t)k0 * A.ld + k0;
+  const bool mine = t < m;
+  T r[PANEL_MAX];
+#pragma unroll
+  for (int c = 0; c < PANEL_MAX; ++c) r[c] = (mine && c < kb) ? g[(int64_t)t * A.ld + c] : zero_v<T>();
+#pragma unroll
+  for (int j = 0; j < PANEL_MAX; ++j) {
+    if (j < kb) {
+      // argmax over rows [j, m) of column j
+      const bool cand = mine && t >= j;
+      const K kv = cand ? pkey(r[j]) : (K)-1;
+      bool bad = cand && (!(kv == kv) || kv == (K)INFINITY);
+      KeyIdx<K> best{kv, cand ? t : 0x7fffffff};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, best.key, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+        best = kmax(best, other);
+      }
+      bad = __syncthreads_or(bad);
+      if ((t & 31) == 0) red[t >> 5] = best;
+      __syncthreads();
+      KeyIdx<K> bb = red[0];
+      if (t == 0) {
+        for (int w = 1; w < PANEL_THREADS / 32; ++w) bb = kmax(bb, red[w]);
+        const int p = (bb.idx == 0x7fffffff) ? j : bb.idx;
+        s_p = p;
+        piv[(int64_t)b * n + k0 + j] = k0 + p;
+      }
+      __syncthreads();
+      const int p = s_p;
+      // swap rows j and p through shared memory
+      if (t == p)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c) prow[c] = r[c];
+      if (t == j && p != j)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c) jrow[c] = r[c];
+      __syncthreads();
+      if (t == j && p != j)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c) r[c] = prow[c];
+      if (t == p && p != j)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c) r[c] = jrow[c];
+      if (t == 0) {
+        const T pv = prow[j];
+        const bool ok = !bad && bb.key > (K)0;
+        s_ok = ok;
+        if (!ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+        s_rinv = ok ? recip_(pv) : one_v<T>();
+      }
+      __syncthreads();
+      if (mine && t > j) {
+        if (s_ok) r[j] = mul_(r[j], s_rinv);
+        const T l = neg_(r[j]);
+#pragma unroll
+        for (int c = j + 1; c < PANEL_MAX; ++c)
+          if (c < kb) mac(r[c], l, prow[c]);
+      }
+      __syncthreads();  // prow / jrow are rewritten by the next column
+    }
+  }
+  if (mine)
+#pragma unroll
+    for (int c = 0; c < PANEL_MAX; ++c)
+      if (c < kb) g[(int64_t)t * A.ld + c] = r[c];
+}
+
+
 template <typename T> constexpr size_t laswp_trsm_smem() {
   return sizeof(T) * (size_t)(PANEL_MAX * (PANEL_MAX + 1) + PANEL_MAX * (TB + 1));
 }

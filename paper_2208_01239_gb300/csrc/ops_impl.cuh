@@ -241,8 +241,13 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
     const int kb = std::min(nb, n - k0);
     const size_t bytes = (size_t)(n - k0) * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
-    FROB_LAUNCH(getrf_panel_name<T>(), st, getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info, info_off,
-                                                                            staged));
+    if (n - k0 <= PANEL_THREADS && sizeof(T) <= 8)
+      FROB_LAUNCH(getrf_panel_name<T>(), st,
+                  getrf_panel_reg_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(n, k0, kb, A, piv, info, info_off));
+    else
+      FROB_LAUNCH(getrf_panel_name<T>(), st,
+                  getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info,
+                                                                                         info_off, staged));
     FROB_LAUNCH(laswp_name<T>(), st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
     const int r = k0 + kb;
     if (r < n) {
