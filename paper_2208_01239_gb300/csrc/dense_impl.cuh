@@ -207,8 +207,12 @@ template <typename R> struct EpiFrobOut {
 // for k > i).
 template <typename T, int OPA, int OPB, class Epi>
 __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<const T> A, MatB<const T> B, Epi epi,
-                                                   int tile_mode) {
-  const int b = blockIdx.z;
+                                                   int tile_mode, int npairs, int shift) {
+  // blockIdx.z = matrix * npairs + pair: pair p moves every operand and the
+  // output p * shift rows and columns down the diagonal (several equal
+  // diagonal-block problems of one matrix in one launch)
+  const int b = blockIdx.z / npairs;
+  const int64_t dsh = (int64_t)(blockIdx.z % npairs) * shift;
   const int i0 = blockIdx.y * TB, j0 = blockIdx.x * TB;
   if ((tile_mode & 1) && j0 > i0 + TB - 1) return;
   __shared__ SmemAB<T> sm;
@@ -220,14 +224,15 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
   int kbeg = (tile_mode & 2) ? (i0 > j0 ? i0 : j0) : 0;
   if ((tile_mode & 4) && j0 > kbeg) kbeg = j0;
   const int kend = ((tile_mode & 8) && i0 + TB < K) ? i0 + TB : K;
-  mainloop<T, OPA, OPB>(acc, sm, A.at(b), A.ld, B.at(b), B.ld, M, N, i0, j0, kbeg, kend);
+  mainloop<T, OPA, OPB>(acc, sm, A.at(b) + dsh * (A.ld + 1), A.ld, B.at(b) + dsh * (B.ld + 1), B.ld, M, N, i0, j0,
+                        kbeg, kend);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       int i = i0 + 4 * ty + r, j = j0 + 4 * tx + c;
-      if (i < M && j < N) epi(b, i, j, acc[r][c]);
+      if (i < M && j < N) epi(b, (int)(i + dsh), (int)(j + dsh), acc[r][c]);
     }
 }
 

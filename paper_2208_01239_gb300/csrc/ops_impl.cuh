@@ -135,12 +135,13 @@ template <typename T> inline int panel_width() { return PANEL_MAX; }
 
 template <typename T, int OPA, int OPB, class Epi>
 inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<const T> B, Epi epi, int tile_mode,
-                        cudaStream_t st) {
+                        cudaStream_t st, int npairs = 1, int shift = 0) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch);
+  dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch * npairs);
   static const std::string name = std::string("gemm<") + type_tag<T>() + ",op" + std::to_string(OPA) + ",op" +
                                   std::to_string(OPB) + "," + Epi::tag + ">";
-  FROB_LAUNCH(name.c_str(), st, gemm_kernel<T, OPA, OPB, Epi><<<grid, NTH, 0, st>>>(M, N, K, A, B, epi, tile_mode));
+  FROB_LAUNCH(name.c_str(), st,
+              gemm_kernel<T, OPA, OPB, Epi><<<grid, NTH, 0, st>>>(M, N, K, A, B, epi, tile_mode, npairs, shift));
 }
 
 template <typename T>
@@ -201,16 +202,22 @@ inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cu
   FROB_LAUNCH(name.c_str(), st,
               trtri_diag_kernel<T, UNIT><<<dim3(nblk, 1, batch), NTH, sizeof(SmemTrsm<T>), st>>>(n, Lm, X));
   auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
+  // the pairs of one level with full-size C in one launch (pair p is pair 0
+  // moved 2 s p down the diagonal), a short last pair on its own
+  auto join = [&](int r, int s, int sc, int npairs) {
+    MatB<const T> B = Lm.sub(r + s, r);
+    MatB<T> Tp = Tmp.sub(r + s, r);
+    gemm_launch<T, OP_N, OP_N>(sc, s, s, batch, B, cst(X.sub(r, r)), axpby<T>(Tp, one_v<T>(), zero_v<T>(), true), 4,
+                               st, npairs, 2 * s);                                        // B A^{-1}
+    gemm_launch<T, OP_N, OP_N>(sc, s, sc, batch, cst(X.sub(r + s, r + s)), cst(Tp),
+                               axpby<T>(X.sub(r + s, r), neg_(one_v<T>()), zero_v<T>(), true), 8, st, npairs,
+                               2 * s);                                                    // -C^{-1} (B A^{-1})
+  };
   for (int s = TB; s < n; s *= 2) {
-    for (int r = 0; r + s < n; r += 2 * s) {
-      const int sc = (n - r - s) < s ? (n - r - s) : s;  // order of C (the last one may be short)
-      MatB<const T> B = Lm.sub(r + s, r);
-      MatB<T> Tp = Tmp.sub(r + s, r);
-      gemm_launch<T, OP_N, OP_N>(sc, s, s, batch, B, cst(X.sub(r, r)), axpby<T>(Tp, one_v<T>(), zero_v<T>(), true), 4,
-                                 st);                                                     // B A^{-1}
-      gemm_launch<T, OP_N, OP_N>(sc, s, sc, batch, cst(X.sub(r + s, r + s)), cst(Tp),
-                                 axpby<T>(X.sub(r + s, r), neg_(one_v<T>()), zero_v<T>(), true), 8, st);  // -C^{-1} (B A^{-1})
-    }
+    const int full = n / (2 * s);              // pairs [2 s p, 2 s p + 2 s) inside the matrix
+    if (full > 0) join(0, s, s, full);
+    const int r = full * 2 * s;                // a last pair with a short C
+    if (r + s < n) join(r, s, n - r - s, 1);
   }
 }
 
