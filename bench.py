@@ -34,6 +34,10 @@ SEED = 2
 WORKLOAD = "hpd_batch64_n512_fp64"
 METRIC = "complex inversions/s (Frobenius-Cholesky vs complex Cholesky), 1 GB300, equal residual"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s
+# DRAM bytes (read + write) of one launch of the final product with the
+# interleaving epilogue (32 matrices of order 512), from one ncu capture of
+# the current kernel: profiles/gemm_frobout_f64_hpd_b64_n512.md
+TRAFFIC_PER_LAUNCH = {"gemm<f64,op0,op0,frob_out>": 225.8e6}
 
 
 def algorithmic_flops(n, batch):
@@ -457,7 +461,8 @@ def main():
         launches_top, ms_top = prof[top]
         ach = alg[top] * args.steps / (ms_top * 1e-3) / 1e12
         roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS, launches_per_step=launches_top / args.steps,
-                    flops_per_step=alg[top], ms_per_launch=ms_top / launches_top)
+                    flops_per_step=alg[top], ms_per_launch=ms_top / launches_top,
+                    traffic=TRAFFIC_PER_LAUNCH.get(top))
 
     exec_flops = flops.executed("frob_chol", N_ORDER) * BATCH
     tflops_exec = exec_flops / (ms_per_step * 1e-3) / 1e12
