@@ -78,9 +78,16 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, i
                          S::BYTES);
     attr = true;
   }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  // persistent: one CTA per SM (the shared memory admits no second), at most one per tile
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
+  if (tiles > INT32_MAX) return cudaErrorInvalidValue;  // the kernel counts tiles in int
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
   FROB_LAUNCH(KIND == 0 ? "tc_gemm<bf16>" : "tc_gemm<tf32>", st,
-              tc_gemm_kernel<KIND, BN, STAGES, Epi><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K, epi, err));
+              tc_gemm_kernel<KIND, BN, STAGES, Epi><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K, batch, epi,
+                                                                                           err));
   return cudaGetLastError();
 }
 
@@ -130,8 +137,9 @@ extern "C" frob_status frob_gemm_tc(int kind, int M, int N, int K, int batch, co
       !tc::make_map(&mb, wb, kind, K, N, batch, p, (int64_t)N * p, 256))
     return FROB_ERR_CUDA;
   tc::TcEpiStoreF32 epi{C, ldc, sc, 1.f, 0.f};
-  // 128 x 256 output tiles: the widest UMMA N for cta_group::1 (measured
-  // 1142 TFLOP/s BF16 at 8192^3 against 800 for 128 x 128 tiles)
+  // 128 x 256 output tiles: the widest UMMA N for cta_group::1; persistent
+  // CTAs with two TMEM accumulators overlap each tile's epilogue with the
+  // next tile's main loop
   cudaError_t e = kind == 0 ? tc::launch<0, 256, 4>(ma, mb, M, N, K, batch, epi, err, st)
                             : tc::launch<1, 256, 4>(ma, mb, M, N, K, batch, epi, err, st);
   return e == cudaSuccess ? FROB_OK : FROB_ERR_CUDA;

@@ -13,7 +13,9 @@
 // (one elected lane) issues tcgen05.mma, committing each stage back to the
 // producer through an mbarrier; warps 2..5 read the 128 x BN FP32 accumulator
 // out of TMEM (warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31) and run the
-// epilogue.  One output tile of 128 x BN per CTA.
+// epilogue.  The kernel is persistent (one CTA per SM, tiles strided by the
+// grid) and TMEM holds two accumulators, so that the epilogue of one tile
+// runs while the tensor core computes the next.
 //
 // Every wait on an mbarrier is bounded by the global timer: a wait that runs
 // out sets an error flag (the caller's `err` word) and the thread stops
@@ -167,35 +169,46 @@ struct TcEpiStoreF32 {
   }
 };
 
+// Persistent: CTA c takes output tiles c, c + gridDim.x, ... (x fastest, then
+// y, then the batch).  TMEM holds two BN-column accumulators; the MMA issuer
+// fills one while the epilogue warps drain the other, so a tile's epilogue
+// overlaps the next tile's main loop.
 template <int KIND, int BN, int STAGES, class Epi>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-                   int K, Epi epi, int* err) {
+                   int K, int batch, Epi epi, int* err) {
   using S = TcSmem<BN, STAGES>;
   constexpr int ELEM = (KIND == 0) ? 2 : 4;
   constexpr int BK = BK_BYTES / ELEM;          // K elements per stage (64 BF16 / 32 TF32)
   constexpr int MMA_K = 32 / ELEM;             // K per instruction (16 BF16 / 8 TF32)
   constexpr uint32_t IDESC = instr_desc<KIND, BN>();
-  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t ACC_COLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
 
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * S::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* acc_full = empty + STAGES;  // [2]
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.z;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kblocks = (K + BK - 1) / BK;
+  const int nx = (N + BN - 1) / BN, ny = (M + BM - 1) / BM;
+  const int ntiles = nx * ny * batch;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);  // the four epilogue warps
+    }
+    mbar_init(mma_done, 1);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -206,64 +219,93 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  int filled = 0;  // producer: stages filled
 
   if (warp == 0) {
     if (lane == 0) {
       // producer
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t round = kb / STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) {
-          atomicExch(err, FROB_ERR_TIMEOUT);
-          break;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int xt = t % nx, yt = (t / nx) % ny, b = t / (nx * ny);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          const int s = filled % STAGES;
+          if (filled >= STAGES && !mbar_wait(&empty[s], ((filled / STAGES) - 1) & 1)) {
+            atomicExch(err, FROB_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          unsigned char* sa = base + s * S::STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+          tma_load_3d(sa, &mapA, &full[s], kb * BK, yt * BM, b);
+          tma_load_3d(sa + S::A_BYTES, &mapB, &full[s], kb * BK, xt * BN, b);
+          ++filled;
         }
-        unsigned char* sa = base + s * S::STAGE_BYTES;
-        mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
-        tma_load_3d(sa, &mapA, &full[s], kb * BK, m0, b);
-        tma_load_3d(sa + S::A_BYTES, &mapB, &full[s], kb * BK, n0, b);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
       bool ok = true;
-      for (int kb = 0; kb < kblocks && ok; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+      int used = 0;  // stages consumed
+      int it = 0;    // tiles of this CTA
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (it >= 2 && !mbar_wait(&acc_empty[buf], ((it >> 1) - 1) & 1)) {
           atomicExch(err, FROB_ERR_TIMEOUT);
-          ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t sa = smem_u32(base + s * S::STAGE_BYTES);
-        const uint32_t sb = sa + S::A_BYTES;
+        const uint32_t acc = tmem + (uint32_t)(buf * ACC_COLS);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          const int s = used % STAGES;
+          if (!mbar_wait(&full[s], (used / STAGES) & 1)) {
+            atomicExch(err, FROB_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(base + s * S::STAGE_BYTES);
+          const uint32_t sb = sa + S::A_BYTES;
 #pragma unroll
-        for (int k = 0; k < BK / MMA_K; ++k) {
-          const uint64_t ad = sw128_desc(sa + k * 32);
-          const uint64_t bd = sw128_desc(sb + k * 32);
-          mma<KIND>(tmem, ad, bd, IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < BK / MMA_K; ++k) {
+            const uint64_t ad = sw128_desc(sa + k * 32);
+            const uint64_t bd = sw128_desc(sb + k * 32);
+            mma<KIND>(acc, ad, bd, IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);
+          ++used;
         }
-        mma_commit(&empty[s]);
+        if (ok) mma_commit(&acc_full[buf]);
       }
-      mma_commit(done);
+      // every MMA this thread issued has finished before TMEM is released
+      mma_commit(mma_done);
+      if (!mbar_wait(mma_done, 0)) atomicExch(err, FROB_ERR_TIMEOUT);
     }
   } else {
     // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ...
     const int sub = warp & 3;
-    const int row = m0 + sub * 32 + lane;
-    const bool ok = mbar_wait(done, 0);
-    if (!ok && lane == 0) atomicExch(err, FROB_ERR_TIMEOUT);
-    tc_fence_after();
-    if (ok) {
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int xt = t % nx, yt = (t / nx) % ny, b = t / (nx * ny);
+      const int buf = it & 1;
+      if (!mbar_wait(&acc_full[buf], (it >> 1) & 1)) {
+        if (lane == 0) atomicExch(err, FROB_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int row = yt * BM + sub * 32 + lane;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)c, v);
-        const int col0 = n0 + c;
+        tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(buf * ACC_COLS + c), v);
+        const int col0 = xt * BN + c;
         int nvalid = N - col0;
         nvalid = nvalid > 16 ? 16 : nvalid;
         if (row < M && nvalid > 0) epi(b, row, col0, v, nvalid);
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
   }
   tc_fence_before();
@@ -271,10 +313,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   // the producer waits for any stage it filled that the MMA did not consume,
   // so that no TMA write lands in shared memory after the CTA exits
   if (warp == 0 && lane == 0) {
-    for (int s = 0; s < STAGES && s < kblocks; ++s) {
-      const int last = ((kblocks - 1 - s) / STAGES) * STAGES + s;  // last k-block that used stage s
-      mbar_wait(&full[s], (last / STAGES) & 1);
-    }
+    for (int j = (filled > STAGES ? filled - STAGES : 0); j < filled; ++j)
+      mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
   }
   if (warp == 1) {
     tc_fence_after();

@@ -34,7 +34,10 @@ def round_tf32(x):
 
 @pytest.mark.parametrize("kind", ["bf16", "tf32"])
 @pytest.mark.parametrize("shape", [(128, 128, 64, 1), (256, 384, 512, 2), (200, 130, 100, 3), (1, 1, 1, 1),
-                                   (129, 257, 1000, 1), (512, 512, 512, 4)])
+                                   (129, 257, 1000, 1), (512, 512, 512, 4),
+                                   # more tiles than SMs: persistent CTAs take several tiles each and
+                                   # reuse both TMEM accumulators
+                                   (1100, 2300, 192, 2), (2048, 2048, 128, 3)])
 def test_tc_gemm_exact_operands(F, kind, shape):
     M, N, K, batch = shape
     g = np.random.default_rng(M * 7 + N * 3 + K)
