@@ -31,6 +31,9 @@
 //                      A = L L^H): the diagonal block by one warp in
 //                      registers (redone by every CTA), then the rows below
 //                      it, L21 = A21 L11^{-H}, one thread per row.
+//   potrf_small_kernel the whole Cholesky of a real FP32 matrix with n <= 512
+//                      by one CTA (panels, row solves and trailing updates
+//                      between CTA barriers).
 //   mirror_kernel      completes a symmetric / Hermitian matrix from its
 //                      lower tiles.
 #pragma once
@@ -789,6 +792,172 @@ __global__ void __launch_bounds__(128) potrf_panel_kernel(int n, int k0, int kb,
 #pragma unroll
   for (int j = 0; j < PANEL_MAX; ++j)
     if (j < kb) a[j] = x[j];
+}
+
+// Whole-matrix Cholesky (lower, A = L L^T, in place) of a real FP32 matrix
+// with n <= SCHOL_MAX by one CTA of SCHOL_THREADS threads, for the batched
+// sizes where one CTA per matrix is enough work: it replaces the 2 n / 32
+// launches of the blocked form.  Per 32-wide panel [k0, k0 + 32):
+//   1. the panel's rows k0 .. n - 1 are copied into shared memory (P, row
+//      pitch 33; 16-byte loads, eight lanes per 128-byte row, when the rows
+//      are 16-byte aligned);
+//   2. warp 0 factors the diagonal block from P in registers (chol32_warp);
+//      a non-positive or non-finite pivot is reported as in
+//      potrf_panel_kernel, with a unit pivot in its place;
+//   3. thread t solves row 32 + t of P, x L11^T = a, column by column
+//      (independent FMAs), and also keeps it transposed in Lt;
+//   4. P goes back to global memory (the diagonal block's lower triangle
+//      and the rows below it), and the 16 warps update the lower 32 x 32
+//      tiles of the trailing matrix, A22 -= L21 L21^T: lane (ty, tx) of a
+//      warp holds rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 and
+//      16 + 4 tx .. 16 + 4 tx + 3 of its tile in registers, read from Lt as
+//      broadcast float4s, so that each row's 8 entries are two 16-byte
+//      chunks contiguous across the lanes in global memory.
+// Entries above the diagonal are not written.  Grid: batch.
+constexpr int SCHOL_MAX = 512;
+constexpr int SCHOL_THREADS = 512;
+constexpr int SCHOL_PP = PANEL_MAX + 1;        // row pitch of P
+constexpr int SCHOL_LTP = SCHOL_MAX - 32 + 4;  // row pitch of Lt (rows below the first panel)
+constexpr int SCHOL_SMEM = (PANEL_MAX * SCHOL_LTP + SCHOL_MAX * SCHOL_PP + 2 * PANEL_MAX) * 4;
+
+template <typename T>  // float
+__global__ void __launch_bounds__(SCHOL_THREADS, 1) potrf_small_kernel(int n, MatB<T> A, frob_info* info,
+                                                                       int info_off) {
+  static_assert(sizeof(T) == 4 && T(0.5f) == 0.5f, "real FP32 only");
+  extern __shared__ float4 schol_raw[];
+  float* Lt = reinterpret_cast<float*>(schol_raw);  // Lt[c * SCHOL_LTP + r] = L[k0 + 32 + r][k0 + c]
+  float* P = Lt + PANEL_MAX * SCHOL_LTP;            // P[r * SCHOL_PP + c] = A[k0 + r][k0 + c]
+  float* dinv = P + SCHOL_MAX * SCHOL_PP;
+  float* colj = dinv + PANEL_MAX;
+  const int b = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  float* Ab = A.at(b);
+  const int64_t ld = A.ld;
+  const bool vec = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(Ab) & 15) == 0;
+  for (int k0 = 0; k0 < n; k0 += PANEL_MAX) {
+    const int kb = n - k0 < PANEL_MAX ? n - k0 : PANEL_MAX;
+    const int r0 = k0 + kb;
+    const int m = n - r0;  // rows below the panel (kb = 32 whenever m > 0)
+    const int pr = n - k0;  // rows of P
+    // 1. panel -> P
+    if (vec && kb == PANEL_MAX) {
+      for (int e = t; e < pr * 8; e += SCHOL_THREADS) {
+        const int r = e >> 3, q = e & 7;
+        const float4 v = *reinterpret_cast<const float4*>(Ab + (int64_t)(k0 + r) * ld + k0 + 4 * q);
+        float* d = P + r * SCHOL_PP + 4 * q;
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+      }
+    } else {
+      for (int e = t; e < pr * PANEL_MAX; e += SCHOL_THREADS) {
+        const int r = e >> 5, c = e & 31;
+        P[r * SCHOL_PP + c] = c < kb ? Ab[(int64_t)(k0 + r) * ld + k0 + c] : 0.f;
+      }
+    }
+    __syncthreads();
+    // 2. diagonal block
+    if (warp == 0) {
+      float rr[PANEL_MAX];
+      int fail;
+      chol32_warp<float>(P, SCHOL_PP, kb, colj, rr, &fail);
+      if (fail >= 0 && lane == 0) report(info, b, FROB_ERR_NOT_HPD, info_off + k0 + fail + 1);
+#pragma unroll
+      for (int c = 0; c < PANEL_MAX; ++c) P[lane * SCHOL_PP + c] = rr[c];
+      if (lane < kb) dinv[lane] = 1.f / rr[lane];
+    }
+    __syncthreads();
+    // 3. rows below it
+    if (t < m) {
+      float x[PANEL_MAX];
+      float* pr_t = P + (PANEL_MAX + t) * SCHOL_PP;
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j) x[j] = pr_t[j];
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j) {
+        x[j] *= dinv[j];
+#pragma unroll
+        for (int i = j + 1; i < PANEL_MAX; ++i) x[i] = fmaf(-x[j], P[i * SCHOL_PP + j], x[i]);
+      }
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j) {
+        pr_t[j] = x[j];
+        Lt[j * SCHOL_LTP + t] = x[j];
+      }
+    }
+    __syncthreads();
+    // 4. P -> panel (lower triangle of the diagonal block, full rows below)
+    if (vec && kb == PANEL_MAX) {
+      for (int e = t; e < pr * 8; e += SCHOL_THREADS) {
+        const int r = e >> 3, q = e & 7;
+        const float* sp = P + r * SCHOL_PP + 4 * q;
+        float* g = Ab + (int64_t)(k0 + r) * ld + k0 + 4 * q;
+        if (r >= PANEL_MAX || 4 * q + 3 <= r) {
+          *reinterpret_cast<float4*>(g) = make_float4(sp[0], sp[1], sp[2], sp[3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (4 * q + c <= r) g[c] = sp[c];
+        }
+      }
+    } else {
+      for (int e = t; e < pr * PANEL_MAX; e += SCHOL_THREADS) {
+        const int r = e >> 5, c = e & 31;
+        if (c < kb && (r >= PANEL_MAX || c <= r)) Ab[(int64_t)(k0 + r) * ld + k0 + c] = P[r * SCHOL_PP + c];
+      }
+    }
+    if (m <= 0) break;
+    const int mt = (m + 31) >> 5;
+    const int ntile = mt * (mt + 1) / 2;
+    const int ty = lane >> 2, tx = lane & 3;
+    for (int tile = warp; tile < ntile; tile += SCHOL_THREADS / 32) {
+      int I = 0;
+      while ((I + 1) * (I + 2) / 2 <= tile) ++I;  // tile = I (I + 1) / 2 + J, J <= I
+      const int J = tile - I * (I + 1) / 2;
+      const int rb = 32 * I + 4 * ty, cb = 32 * J + 4 * tx;  // columns cb .. cb + 3, cb + 16 .. cb + 19
+      float acc[4][8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < PANEL_MAX; ++c) {
+        const float4 rv = *reinterpret_cast<const float4*>(Lt + c * SCHOL_LTP + rb);
+        const float4 c0 = *reinterpret_cast<const float4*>(Lt + c * SCHOL_LTP + cb);
+        const float4 c1 = *reinterpret_cast<const float4*>(Lt + c * SCHOL_LTP + cb + 16);
+        const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+        const float ca[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ra[i], ca[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = rb + i;
+        if (row >= m) continue;
+        float* dst = Ab + (int64_t)(r0 + row) * ld + r0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = cb + 16 * h;
+          if (vec && col + 3 <= row) {  // all four in range and on or below the diagonal
+            float4 v = *reinterpret_cast<const float4*>(dst + col);
+            v.x -= acc[i][4 * h];
+            v.y -= acc[i][4 * h + 1];
+            v.z -= acc[i][4 * h + 2];
+            v.w -= acc[i][4 * h + 3];
+            *reinterpret_cast<float4*>(dst + col) = v;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (col + j <= row) dst[col + j] -= acc[i][4 * h + j];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace frob

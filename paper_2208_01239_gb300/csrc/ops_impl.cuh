@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -270,7 +271,8 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
 // Blocked right-looking Cholesky (A = L L^H, lower triangle, in place): per
 // 32-wide panel, one launch for the diagonal block and the rows below it (the
 // block factored by one warp of every CTA, the rows one thread each), then
-// the trailing update of the lower tiles.
+// the trailing update of the lower tiles.  Real FP32 matrices with n <= 512
+// take one launch instead, one CTA per matrix (potrf_small_kernel).
 template <typename T> inline const char* potrf_panel_name() {
   static const std::string s = std::string("potrf_panel<") + type_tag<T>() + ">";
   return s.c_str();
@@ -278,6 +280,19 @@ template <typename T> inline const char* potrf_panel_name() {
 
 template <typename T>
 inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (n <= SCHOL_MAX) {
+      // one CTA per matrix (its panels, row solves and trailing updates between CTA barriers)
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(potrf_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCHOL_SMEM);
+        attr = true;
+      }
+      FROB_LAUNCH("potrf_small<f32>", st,
+                  potrf_small_kernel<float><<<batch, SCHOL_THREADS, SCHOL_SMEM, st>>>(n, A, info, info_off));
+      return;
+    }
+  }
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);

@@ -47,7 +47,8 @@
 // (|scaled product| < 2^11), and the sum is converted to FP64 once:
 //   RESID:  writes R^T with R = I - A B (transposed store, coalesced) and
 //           adds sum |R_ij|^2 into a per-matrix FP64 accumulator.
-//   CORR:   X <- X + A B, written to X (row-major) and X^T.
+//   CORR:   X <- X + A B, written to X (row-major) and X^T; the old value is
+//           read from X^T, whose accesses are coalesced across the lanes.
 #pragma once
 
 
@@ -540,16 +541,45 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0 && ss != 0.0) atomicAdd(args.rnorm2 + b, ss);
       } else if (row < n) {
+        // The old value comes from X^T (equal to X entry for entry, and
+        // coalesced across the warp's rows); each batch of CB loads is issued
+        // before any store (more would spill at the 168-register cap of ten
+        // warps).  X itself is written with 32-byte stores, one full sector
+        // of four columns of a row per lane, when n allows.
         double* Xp = args.X + ((int64_t)part * batch + b) * nn;
         double* XTp = args.XT + ((int64_t)part * batch + b) * nn;
+        const bool vec = (n & 3) == 0;
+        constexpr int CB = 4;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-          const int col = c_base + c;
-          if (col < n) {
-            float pf;
-            const double v = Xp[(int64_t)row * n + col] + i64_ldexp(acc[c], ea + __ldg(eB + col) - 52, &pf);
-            Xp[(int64_t)row * n + col] = v;
-            XTp[(int64_t)col * n + row] = v;
+        for (int c0 = 0; c0 < 64; c0 += CB) {
+          double v[CB];
+#pragma unroll
+          for (int i = 0; i < CB; ++i) {
+            const int col = c_base + c0 + i;
+            v[i] = col < n ? XTp[(int64_t)col * n + row] : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < CB; ++i) {
+            const int col = c_base + c0 + i;
+            if (col < n) {
+              float pf;
+              v[i] += i64_ldexp(acc[c0 + i], ea + __ldg(eB + col) - 52, &pf);
+              XTp[(int64_t)col * n + row] = v[i];
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < CB; i += 4) {
+            const int col = c_base + c0 + i;
+            double* dst = Xp + (int64_t)row * n + col;
+            if (vec && col < n) {
+              asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "d"(v[i]), "d"(v[i + 1]),
+                           "d"(v[i + 2]), "d"(v[i + 3])
+                           : "memory");
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (col + q < n) dst[q] = v[i + q];
+            }
           }
         }
       }

@@ -161,7 +161,7 @@ def test_hpd_reads_lower_triangle_only(F):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("n", [7, 64, 100])
+@pytest.mark.parametrize("n", [7, 32, 33, 64, 100, 130, 300])
 def test_hpd_fp32(F, n):
     ms = W.hpd(n, batch=2, seed=4500 + n, lam_hi=1e2).astype(np.complex64)
     x = F.frob_inv_hpd(_dev(ms, "fp32"), prec="fp32").x.cpu().numpy().astype(np.complex128)
@@ -275,6 +275,39 @@ def test_not_hpd_reported(F):
         info = f(_dev(ms), check=False).info()
         assert list(info["status"]) == [F.FROB_OK, F.FROB_ERR_NOT_HPD, F.FROB_OK]
         assert info["bad_index"][1] >= 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_not_hpd_later_panel(F, prec):
+    """A real symmetric A = [[P, C], [C^T, C^T P^-1 C - I]] with P (50 x 50)
+    SPD: the Cholesky pivots 1..50 are positive and pivot 51 is -1 (the Schur
+    complement is -I), so the first failure is reported at index 51, in the
+    second 32-wide panel."""
+    n, k = 100, 50
+    g = np.random.default_rng(31)
+    q, _ = np.linalg.qr(g.standard_normal((k, k)))
+    p = (q * np.linspace(1.0, 4.0, k)) @ q.T
+    c = g.standard_normal((k, n - k)) * 0.3
+    d = c.T @ np.linalg.solve(p, c) - np.eye(n - k)
+    a = np.block([[p, c], [c.T, d]])
+    ms = np.stack([W.hpd(n, 1, seed=5)[0], a.astype(np.complex128)])
+    if prec == "fp32":
+        ms = ms.astype(np.complex64)
+    info = F.frob_inv_hpd(_dev(ms, prec), prec=prec, check=False).info()
+    assert list(info["status"]) == [F.FROB_OK, F.FROB_ERR_NOT_HPD]
+    assert info["bad_index"][1] == k + 1
+
+
+def test_hpd_fp32_n512_closed_form(F):
+    """n = 512 in FP32 (the one-CTA Cholesky at its largest size) against
+    the closed-form inverse Q diag(1/lam) Q^H."""
+    ms, qs, lams = W.hpd(512, batch=3, seed=4600, lam_hi=1e2, return_parts=True)
+    x = F.frob_inv_hpd(_dev(ms.astype(np.complex64), "fp32"), prec="fp32").x.cpu().numpy().astype(np.complex128)
+    for b in range(3):
+        m64 = ms[b].astype(np.complex64).astype(np.complex128)
+        exact = W.hpd_exact_inverse(qs[b], lams[b])
+        assert metrics.forward_error(x[b], exact) <= _fe_bound(m64, "fp32")
+        assert metrics.residual_fro(m64, x[b]) <= RES_GATE["fp32"]
 
 
 def test_argument_errors(F):
