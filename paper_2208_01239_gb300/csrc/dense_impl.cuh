@@ -34,6 +34,9 @@
 //   potrf_small_kernel the whole Cholesky of a real FP32 matrix with n <= 512
 //                      by one CTA (panels, row solves and trailing updates
 //                      between CTA barriers).
+//   getrf_small_kernel the whole LU with partial pivoting of a real FP32
+//                      matrix with n <= 512 by one CTA (rows addressed
+//                      through a permutation, gathered at the end).
 //   mirror_kernel      completes a symmetric / Hermitian matrix from its
 //                      lower tiles.
 #pragma once
@@ -954,6 +957,319 @@ __global__ void __launch_bounds__(SCHOL_THREADS, 1) potrf_small_kernel(int n, Ma
               if (col + j <= row) dst[col + j] -= acc[i][4 * h + j];
           }
         }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Whole-matrix LU with partial pivoting (A = P^T L U, in place, L unit lower,
+// LAPACK-style swap list piv) of a real FP32 matrix with n <= SLU_MAX by one
+// CTA of SLU_THREADS threads.  Rows are not moved in global memory while the
+// factorization runs: perm[i] is the global row that holds logical row i, and
+// the rows are gathered into logical order once at the end.  Per 32-wide
+// panel [k0, k0 + 32):
+//   1. the panel's logical rows k0 .. n - 1 are copied into shared memory P
+//      (row r of P = logical row k0 + r at the start of the panel);
+//   2. column by column, with one CTA barrier per column: thread t keeps
+//      logical row k0 + t in registers.  The pivot is the entry of largest
+//      modulus (ties to the lower row, NaN never chosen), found by an
+//      integer maximum of the keys (bit pattern of |x| plus one, 0 for rows
+//      above the column and for NaN) and a ballot, within each warp and
+//      then over the 16 warp results; each warp's leading row is written to
+//      shared memory before the barrier, so that after it the pivot row is
+//      there for every row below it, which scales its multiplier and
+//      updates the rest of its panel row.  A zero, NaN or infinite pivot column is reported as
+//      FROB_ERR_SINGULAR (bad_index = its 1-based index + info_off) and the
+//      elimination continues unscaled, as in getrf_panel_reg_kernel;
+//   3. the panel goes back to global memory through P, L21 is kept
+//      transposed in Lt, and thread t forms column r0 + t of
+//      U12 = L11^{-1} A12 (kept in Ut, then written row by row);
+//   4. the 16 warps update the trailing matrix, A22 -= L21 U12, in 32 x 16
+//      tiles, each lane a 4 x 4 block in registers from broadcast float4
+//      reads of Lt and Ut (the block's old values are loaded before its
+//      FMAs).
+// Grid: batch.
+constexpr int SLU_MAX = 512;
+constexpr int SLU_THREADS = 512;
+constexpr int SLU_PP = PANEL_MAX + 1;       // row pitch of P
+constexpr int SLU_TP = SLU_MAX - 32 + 4;    // row pitch of Lt and Ut
+constexpr int SLU_GW = 64;                  // columns per round of the final gather
+constexpr int SLU_GP = SLU_GW + 4;          // its row pitch
+constexpr int SLU_FLOATS = 2 * PANEL_MAX * SLU_TP + SLU_MAX * SLU_PP + 2 * 16 * PANEL_MAX + 2 * PANEL_MAX;  // Lt, Ut, P, rows
+constexpr int SLU_INTS = SLU_MAX + 3 * 2 * 16;  // perm, redk, redi, redb
+constexpr int SLU_SMEM = (SLU_FLOATS + SLU_INTS) * 4;
+static_assert(SLU_MAX * SLU_GP <= 2 * PANEL_MAX * SLU_TP + SLU_MAX * SLU_PP, "gather buffer (Lt, Ut and P)");
+static_assert(SLU_SMEM <= 232448, "shared memory per CTA");
+
+template <typename T>  // float
+__global__ void __launch_bounds__(SLU_THREADS, 1) getrf_small_kernel(int n, MatB<T> A, int* piv, frob_info* info,
+                                                                     int info_off) {
+  static_assert(sizeof(T) == 4 && T(0.5f) == 0.5f, "real FP32 only");
+  extern __shared__ float4 slu_raw[];
+  float* Lt = reinterpret_cast<float*>(slu_raw);  // Lt[c * SLU_TP + i] = L[r0 + i][k0 + c] (logical rows)
+  float* Ut = Lt + PANEL_MAX * SLU_TP;             // Ut[c * SLU_TP + j] = U[k0 + c][r0 + j]
+  float* P = Ut + PANEL_MAX * SLU_TP;              // P[r * SLU_PP + c]: the panel
+  float* G = Lt;                                   // final gather: [SLU_MAX][SLU_GP] over Lt, Ut and P
+  float* cand_rows = P + SLU_MAX * SLU_PP;         // [2][16][PANEL_MAX] each warp's leading candidate row
+  float* jrow = cand_rows + 2 * 16 * PANEL_MAX;    // [2][PANEL_MAX] row j
+  int* perm = reinterpret_cast<int*>(jrow + 2 * PANEL_MAX);
+  unsigned* redk = reinterpret_cast<unsigned*>(perm + SLU_MAX);  // [2][16] warp maxima of the keys
+  int* redi = reinterpret_cast<int*>(redk + 32);                 // [2][16] their rows (panel-relative)
+  int* redb = redi + 32;                                         // [2][16] NaN / infinity seen
+  static_assert(SLU_FLOATS == 2 * PANEL_MAX * SLU_TP + SLU_MAX * SLU_PP + 2 * 16 * PANEL_MAX + 2 * PANEL_MAX &&
+                    SLU_INTS == SLU_MAX + 3 * 32,
+                "the arrays above fill SLU_FLOATS and SLU_INTS exactly");
+  const int b = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  float* Ab = A.at(b);
+  const int64_t ld = A.ld;
+  const bool vec = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(Ab) & 15) == 0;
+  if (t < n) perm[t] = t;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += PANEL_MAX) {
+    const int kb = n - k0 < PANEL_MAX ? n - k0 : PANEL_MAX;
+    const int m = n - k0;   // panel rows
+    const int r0 = k0 + kb;
+    const int mm = n - r0;  // trailing order (kb = 32 whenever mm > 0)
+    // 1. panel -> P (all loads of a thread issued before its stores)
+    if (vec && kb == PANEL_MAX) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = t + SLU_THREADS * (4 * h + i);
+          if (e < m * 8)
+            v[i] = *reinterpret_cast<const float4*>(Ab + (int64_t)perm[k0 + (e >> 3)] * ld + k0 + 4 * (e & 7));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = t + SLU_THREADS * (4 * h + i);
+          if (e < m * 8) {
+            float* d = P + (e >> 3) * SLU_PP + 4 * (e & 7);
+            d[0] = v[i].x;
+            d[1] = v[i].y;
+            d[2] = v[i].z;
+            d[3] = v[i].w;
+          }
+        }
+      }
+    } else {
+      for (int e = t; e < m * PANEL_MAX; e += SLU_THREADS) {
+        const int r = e >> 5, c = e & 31;
+        P[r * SLU_PP + c] = c < kb ? Ab[(int64_t)perm[k0 + r] * ld + k0 + c] : 0.f;
+      }
+    }
+    __syncthreads();
+    // 2. the panel, column by column, one CTA barrier per column: thread t
+    // keeps logical row k0 + t in registers; before the barrier each warp's
+    // leading candidate row (and row j) is already in shared memory,
+    // double-buffered by column parity.
+    const bool mine = t < m;
+    float rr[PANEL_MAX];
+#pragma unroll
+    for (int c = 0; c < PANEL_MAX; ++c) rr[c] = mine ? P[t * SLU_PP + c] : 0.f;
+#pragma unroll
+    for (int j = 0; j < PANEL_MAX; ++j) {
+      if (j < kb) {
+        const int buf = j & 1;
+        const bool cand = mine && t >= j;
+        const float kv = fabsf(rr[j]);
+        const bool bad = cand && !(kv < INFINITY);  // NaN or infinite
+        const unsigned key = (cand && kv == kv) ? __float_as_uint(kv) + 1u : 0u;
+        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+        const int wl = __ffs(__ballot_sync(0xffffffffu, key == wmax)) - 1;
+        const bool wbad = __any_sync(0xffffffffu, bad);
+        if (lane == wl) {
+          float4* d = reinterpret_cast<float4*>(cand_rows + (buf * 16 + warp) * PANEL_MAX);
+#pragma unroll
+          for (int q = 0; q < PANEL_MAX / 4; ++q) d[q] = make_float4(rr[4 * q], rr[4 * q + 1], rr[4 * q + 2], rr[4 * q + 3]);
+        }
+        if (t == j) {
+          float4* d = reinterpret_cast<float4*>(jrow + buf * PANEL_MAX);
+#pragma unroll
+          for (int q = 0; q < PANEL_MAX / 4; ++q) d[q] = make_float4(rr[4 * q], rr[4 * q + 1], rr[4 * q + 2], rr[4 * q + 3]);
+        }
+        if (lane == 0) {
+          redk[buf * 16 + warp] = wmax;
+          redi[buf * 16 + warp] = warp * 32 + wl;
+          redb[buf * 16 + warp] = wbad ? 1 : 0;
+        }
+        __syncthreads();
+        const unsigned k16 = lane < 16 ? redk[buf * 16 + lane] : 0u;
+        const unsigned gmax = __reduce_max_sync(0xffffffffu, k16);
+        const int ww = __ffs(__ballot_sync(0xffffffffu, lane < 16 && k16 == gmax)) - 1;
+        const bool anybad = __any_sync(0xffffffffu, lane < 16 && redb[buf * 16 + lane] != 0);
+        const int p = gmax == 0u ? j : redi[buf * 16 + ww];
+        const float4* prw =
+            reinterpret_cast<const float4*>(gmax == 0u ? jrow + buf * PANEL_MAX : cand_rows + (buf * 16 + ww) * PANEL_MAX);
+        const bool ok = !anybad && gmax > 1u;  // the largest |x| is above zero
+        if (t == 0) {
+          piv[(int64_t)b * n + k0 + j] = k0 + p;
+          if (!ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+          const int q = perm[k0 + j];
+          perm[k0 + j] = perm[k0 + p];
+          perm[k0 + p] = q;
+        }
+        if ((t == j || t == p) && p != j) {
+          const float4* src = t == j ? prw : reinterpret_cast<const float4*>(jrow + buf * PANEL_MAX);
+#pragma unroll
+          for (int q = 0; q < PANEL_MAX / 4; ++q) {
+            const float4 v = src[q];
+            rr[4 * q] = v.x;
+            rr[4 * q + 1] = v.y;
+            rr[4 * q + 2] = v.z;
+            rr[4 * q + 3] = v.w;
+          }
+        }
+        if (mine && t > j) {
+          float pr[PANEL_MAX];
+#pragma unroll
+          for (int q = j / 4; q < PANEL_MAX / 4; ++q) {
+            const float4 v = prw[q];
+            pr[4 * q] = v.x;
+            pr[4 * q + 1] = v.y;
+            pr[4 * q + 2] = v.z;
+            pr[4 * q + 3] = v.w;
+          }
+          if (ok) rr[j] *= 1.f / pr[j];
+          const float l = -rr[j];
+#pragma unroll
+          for (int c = j + 1; c < PANEL_MAX; ++c)
+            if (c < kb) rr[c] = fmaf(l, pr[c], rr[c]);
+        }
+      }
+    }
+    // 3. the panel back (P, global memory), L21 into Lt, U12 into Ut
+    if (mine) {
+#pragma unroll
+      for (int c = 0; c < PANEL_MAX; ++c) P[t * SLU_PP + c] = rr[c];
+      if (t >= kb)
+#pragma unroll
+        for (int c = 0; c < PANEL_MAX; ++c) Lt[c * SLU_TP + (t - kb)] = rr[c];
+    }
+    __syncthreads();
+    if (vec && kb == PANEL_MAX) {
+      for (int e = t; e < m * 8; e += SLU_THREADS) {
+        const int r = e >> 3, q = e & 7;
+        const float* sp = P + r * SLU_PP + 4 * q;
+        *reinterpret_cast<float4*>(Ab + (int64_t)perm[k0 + r] * ld + k0 + 4 * q) = make_float4(sp[0], sp[1], sp[2], sp[3]);
+      }
+    } else {
+      for (int e = t; e < m * PANEL_MAX; e += SLU_THREADS) {
+        const int r = e >> 5, c = e & 31;
+        if (c < kb) Ab[(int64_t)perm[k0 + r] * ld + k0 + c] = P[r * SLU_PP + c];
+      }
+    }
+    if (mm <= 0) break;
+    if (t < mm) {
+      float x[PANEL_MAX];
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j) x[j] = Ab[(int64_t)perm[k0 + j] * ld + r0 + t];
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j)
+#pragma unroll
+        for (int i = j + 1; i < PANEL_MAX; ++i) x[i] = fmaf(-P[i * SLU_PP + j], x[j], x[i]);
+#pragma unroll
+      for (int j = 0; j < PANEL_MAX; ++j) Ut[j * SLU_TP + t] = x[j];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int j = 0; j < PANEL_MAX; ++j) {  // U12 back to global memory, row by row
+      float* g = Ab + (int64_t)perm[k0 + j] * ld + r0;
+      for (int c = t; c < mm; c += SLU_THREADS) g[c] = Ut[j * SLU_TP + c];
+    }
+    // 4. trailing update A22 -= L21 U12 over 32 x 16 tiles, each lane a
+    // 4 x 4 block (its old values loaded before the FMAs)
+    const int mt = (mm + 31) >> 5, nt = (mm + 15) >> 4;
+    const int ty = lane >> 2, tx = lane & 3;
+    for (int tile = warp; tile < mt * nt; tile += SLU_THREADS / 32) {
+      const int I = tile / nt, J = tile % nt;
+      const int rb = 32 * I + 4 * ty, cb = 16 * J + 4 * tx;
+      const bool cfull = vec && cb + 3 < mm;
+      float old[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = rb + i;
+        const float* src = Ab + (int64_t)perm[r0 + (row < mm ? row : 0)] * ld + r0 + cb;
+        if (row < mm && cfull) {
+          const float4 v = *reinterpret_cast<const float4*>(src);
+          old[i][0] = v.x;
+          old[i][1] = v.y;
+          old[i][2] = v.z;
+          old[i][3] = v.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) old[i][j] = (row < mm && cb + j < mm) ? src[j] : 0.f;
+        }
+      }
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < PANEL_MAX; ++c) {
+        const float4 rv = *reinterpret_cast<const float4*>(Lt + c * SLU_TP + rb);
+        const float4 cv = *reinterpret_cast<const float4*>(Ut + c * SLU_TP + cb);
+        const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+        const float ca[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ra[i], ca[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = rb + i;
+        if (row >= mm) continue;
+        float* dst = Ab + (int64_t)perm[r0 + row] * ld + r0 + cb;
+        if (cfull) {
+          *reinterpret_cast<float4*>(dst) = make_float4(old[i][0] - acc[i][0], old[i][1] - acc[i][1],
+                                                        old[i][2] - acc[i][2], old[i][3] - acc[i][3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (cb + j < mm) dst[j] = old[i][j] - acc[i][j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // rows into logical order, SLU_GW columns at a time (loads before stores)
+  for (int c0 = 0; c0 < n; c0 += SLU_GW) {
+    const int w = n - c0 < SLU_GW ? n - c0 : SLU_GW;
+    if (vec && w == SLU_GW) {
+      float4 v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int e = t + SLU_THREADS * i;  // row e >> 4, 4 columns (e & 15)
+        if (e < n * 16) v[i] = *reinterpret_cast<const float4*>(Ab + (int64_t)perm[e >> 4] * ld + c0 + 4 * (e & 15));
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int e = t + SLU_THREADS * i;
+        if (e < n * 16) *reinterpret_cast<float4*>(G + (e >> 4) * SLU_GP + 4 * (e & 15)) = v[i];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int e = t + SLU_THREADS * i;
+        if (e < n * 16)
+          *reinterpret_cast<float4*>(Ab + (int64_t)(e >> 4) * ld + c0 + 4 * (e & 15)) =
+              *reinterpret_cast<const float4*>(G + (e >> 4) * SLU_GP + 4 * (e & 15));
+      }
+    } else {
+      for (int e = t; e < n * SLU_GW; e += SLU_THREADS) {
+        const int r = e / SLU_GW, c = e % SLU_GW;
+        if (c < w) G[r * SLU_GP + c] = Ab[(int64_t)perm[r] * ld + c0 + c];
+      }
+      __syncthreads();
+      for (int e = t; e < n * SLU_GW; e += SLU_THREADS) {
+        const int r = e / SLU_GW, c = e % SLU_GW;
+        if (c < w) Ab[(int64_t)r * ld + c0 + c] = G[r * SLU_GP + c];
       }
     }
     __syncthreads();

@@ -243,6 +243,19 @@ template <typename T> inline const char* laswp_name() {
 // Blocked right-looking LU with partial pivoting (P A = L U, in place).
 template <typename T>
 inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (n <= SLU_MAX) {
+      // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(getrf_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLU_SMEM);
+        attr = true;
+      }
+      FROB_LAUNCH("getrf_small<f32>", st,
+                  getrf_small_kernel<float><<<batch, SLU_THREADS, SLU_SMEM, st>>>(n, A, piv, info, info_off));
+      return;
+    }
+  }
   panel_smem_attr<T>();
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {

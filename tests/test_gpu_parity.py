@@ -76,7 +76,7 @@ def test_cplx_lu_inv_fp64_vs_oracle(F, n):
         assert metrics.residual_fro(ms[b], x[b]) <= RES_GATE["fp64"]
 
 
-@pytest.mark.parametrize("n", [1, 5, 33, 64, 97, 130])
+@pytest.mark.parametrize("n", [1, 5, 32, 33, 64, 97, 130, 257, 512])
 def test_frob_inv_fp32_vs_oracle(F, n):
     ms = W.gaussian(n, batch=2, seed=3000 + n, dtype=np.complex64)
     x = F.frob_inv(_dev(ms, "fp32"), prec="fp32").x.cpu().numpy().astype(np.complex128)
@@ -245,6 +245,22 @@ def test_almost_sure_singular_real_part(F):
 
 
 # ------------------------------------------------------------------ failures and edge cases
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,k", [(100, 40), (50, 49), (64, 0)])
+def test_zero_column_of_a_reported(F, prec, n, k):
+    """A zero column k of A = Re M stays exactly zero through the elimination
+    of the columns before it (every row has a zero there), so the LU of A
+    meets a zero pivot column at step k + 1, in every precision and panel
+    position."""
+    g = np.random.default_rng(100 + n + k)
+    a = g.standard_normal((n, n))
+    a[:, k] = 0.0
+    m = np.stack([W.gaussian(n, 1, seed=6)[0], a + 1j * g.standard_normal((n, n))])
+    info = F.frob_inv(_dev(m, prec), prec=prec, check=False).info()
+    assert list(info["status"]) == [F.FROB_OK, F.FROB_ERR_SINGULAR]
+    assert int(info["bad_index"][1]) == k + 1
 
 
 def test_singular_inputs_reported(F):
