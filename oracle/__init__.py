@@ -30,6 +30,11 @@ of Dai, Lim and Ye, "Complex matrix inversion via real matrix inversions":
                            inversion" (Sec. 3), several right-hand sides.
 * :func:`sign_newton`   -- Newton's iteration for the matrix sign function
                            (Sec. 5.3, eq. "iter"), fixed step count.
+* :func:`newton`        -- the same iteration, or the polar one (Sec. 5.5,
+                           eq. "iter2"), with the stopping rule of Sec. 5.3.
+* :func:`sylvester`     -- Sylvester equation by the sign of a block matrix
+                           (Sec. 5.4); Lyapunov with B = A^H.
+* :func:`polar`         -- polar decomposition X = Q P (Sec. 5.5).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against values fixed by
 mathematics (closed forms, brute force, identities from the paper, LAPACK via
@@ -123,6 +128,9 @@ class Oracle:
             "orc_inv_adjoint": [i, zp, zp, zp],
             "orc_sign_newton": [i, zp, i, zp],
             "orc_frob_solve": [i, i, zp, zp, zp],
+            "orc_newton": [i, zp, i, ctypes.c_double, i, zp, zp],
+            "orc_sylvester": [i, i, zp, zp, zp, ctypes.c_double, i, zp, zp],
+            "orc_polar": [i, zp, ctypes.c_double, i, zp, zp, zp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -227,6 +235,42 @@ class Oracle:
         _check("sign_newton", self.lib.orc_sign_newton(n, _ptr(m), int(iters), _ptr(out)))
         return out
 
+    def newton(self, m, variant: int, eps: float, kmax: int):
+        """Newton's iteration with the stopping rule of Sec. 5.3: variant 0
+        X <- (X + X^{-1})/2 (sign), variant 1 X <- (X + X^{-H})/2 (polar
+        factor).  Returns (X, steps)."""
+        m, n = _prep(m)
+        out = np.empty_like(m)
+        steps = ctypes.c_int(0)
+        _check("newton", self.lib.orc_newton(n, _ptr(m), int(variant), float(eps), int(kmax), _ptr(out),
+                                             ctypes.byref(steps)))
+        return out, steps.value
+
+    def sylvester(self, a, b, c, eps: float, kmax: int):
+        """Y with A Y + Y B = C through the sign of [[A, -C], [0, -B]]
+        (Sec. 5.4).  Returns (Y, steps)."""
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.complex128))
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.complex128))
+        p, q = a.shape[0], b.shape[0]
+        if a.shape != (p, p) or b.shape != (q, q) or c.shape != (p, q):
+            raise ValueError("shapes: A p x p, B q x q, C p x q")
+        y = np.empty((p, q), dtype=np.complex128)
+        steps = ctypes.c_int(0)
+        _check("sylvester", self.lib.orc_sylvester(p, q, _ptr(a), _ptr(b), _ptr(c), float(eps), int(kmax), _ptr(y),
+                                                   ctypes.byref(steps)))
+        return y, steps.value
+
+    def polar(self, x, eps: float, kmax: int):
+        """X = Q P (Sec. 5.5): Q by Newton's iteration X <- (X + X^{-H})/2,
+        P = Q^H X.  Returns (Q, P, steps)."""
+        x, n = _prep(x)
+        q = np.empty_like(x)
+        pm = np.empty_like(x)
+        steps = ctypes.c_int(0)
+        _check("polar", self.lib.orc_polar(n, _ptr(x), float(eps), int(kmax), _ptr(q), _ptr(pm), ctypes.byref(steps)))
+        return q, pm, steps.value
+
 
 def load(mutant: int = 0) -> Oracle:
     """The oracle bound to the normal build (mutant=0) or a planted-mistake
@@ -278,6 +322,18 @@ def inv_adjoint(x, g):
 
 def sign_newton(m, iters: int):
     return load().sign_newton(m, iters)
+
+
+def newton(m, variant: int, eps: float, kmax: int):
+    return load().newton(m, variant, eps, kmax)
+
+
+def sylvester(a, b, c, eps: float, kmax: int):
+    return load().sylvester(a, b, c, eps, kmax)
+
+
+def polar(x, eps: float, kmax: int):
+    return load().polar(x, eps, kmax)
 
 
 def frob_solve(m, rhs):

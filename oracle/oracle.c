@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORC_MUTANT plants one deliberate mistake (k = 1..10) so that a test can check
+/* ORC_MUTANT plants one deliberate mistake (k = 1..13) so that a test can check
  * that the pins catch it.  Product builds of the oracle use ORC_MUTANT = 0. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -612,6 +612,87 @@ int orc_sign_newton(int n, const zc *m, int iters, zc *out)
         for (size_t t = 0; t < nn; ++t) out[t] = (ORC_MUTANT == 9 ? 1.0 : 0.5) * (out[t] + xi[t]);
     }
     free(xi);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Newton iterations with the stopping rule of Sec. 5.3: X_0 = M, and         */
+/*   variant 0 (matrix sign, eq. "iter"):      X_{k+1} = (X_k + X_k^{-1}) / 2, */
+/*   variant 1 (polar factor, eq. "iter2"):    X_{k+1} = (X_k + X_k^{-H}) / 2, */
+/* stopping after the first step k with ||X_k - X_{k-1}||_max / ||X_k||_max   */
+/* <= eps (max of the entries' moduli), or after kmax steps.  Each inverse is */
+/* the right inverse by complex LU.  *steps receives the number of steps.    */
+/* ------------------------------------------------------------------------- */
+int orc_newton(int n, const zc *m, int variant, double eps, int kmax, zc *out, int *steps)
+{
+    if (n < 1 || kmax < 0 || (variant != 0 && variant != 1)) return -2;
+    size_t nn = (size_t)n * n;
+    zc *xi = malloc(sizeof(zc) * nn);
+    if (!xi) return -1;
+    memcpy(out, m, sizeof(zc) * nn);
+    *steps = 0;
+    for (int k = 1; k <= kmax; ++k) {
+        int info = orc_cplx_lu_inv(n, out, xi, 0);
+        if (info) { free(xi); return info; }
+        double dmax = 0.0, xmax = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                zc inv = (variant == 1 && ORC_MUTANT != 11) ? conj(xi[IDX(j, i)]) : xi[IDX(i, j)];
+                zc nx = 0.5 * (out[IDX(i, j)] + inv);
+                double d = abs2(nx - out[IDX(i, j)]), a = abs2(nx);
+                if (d > dmax) dmax = d;
+                if (a > xmax) xmax = a;
+                out[IDX(i, j)] = nx;
+            }
+        *steps = k;
+        if (sqrt(dmax) <= eps * sqrt(xmax)) break;
+    }
+    free(xi);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sylvester equation A Y + Y B = C (Sec. 5.4), A p x p, B q x q, C p x q:   */
+/* if sign(A) = I_p and sign(B) = I_q, the sign of [[A, -C], [0, -B]] is      */
+/* [[I_p, -2Y], [0, -I_q]]; Newton's iteration (variant 0 above) on that      */
+/* block matrix, then Y = -1/2 times the top-right block of the limit.        */
+/* ------------------------------------------------------------------------- */
+int orc_sylvester(int p, int q, const zc *a, const zc *b, const zc *c, double eps, int kmax, zc *y, int *steps)
+{
+    if (p < 1 || q < 1) return -2;
+    const int n = p + q;
+    zc *x0 = calloc((size_t)n * n, sizeof(zc)), *xs = malloc(sizeof(zc) * (size_t)n * n);
+    if (!x0 || !xs) { free(x0); free(xs); return -1; }
+    for (int i = 0; i < p; ++i) {
+        for (int j = 0; j < p; ++j) x0[IDX(i, j)] = a[(size_t)i * p + j];
+        for (int j = 0; j < q; ++j) x0[IDX(i, p + j)] = -c[(size_t)i * q + j];
+    }
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) x0[IDX(p + i, p + j)] = -b[(size_t)i * q + j];
+    int info = orc_newton(n, x0, 0, eps, kmax, xs, steps);
+    if (info == 0)
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < q; ++j) y[(size_t)i * q + j] = (ORC_MUTANT == 12 ? 0.5 : -0.5) * xs[IDX(i, p + j)];
+    free(x0);
+    free(xs);
+    return info;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Polar decomposition X = Q P (Sec. 5.5): Q by Newton's iteration variant 1  */
+/* above from X_0 = X, then P = Q^H X.                                        */
+/* ------------------------------------------------------------------------- */
+int orc_polar(int n, const zc *x, double eps, int kmax, zc *q, zc *pm, int *steps)
+{
+    int info = orc_newton(n, x, 1, eps, kmax, q, steps);
+    if (info) return info;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            zc s = 0.0;
+            for (int k = 0; k < n; ++k) s += (ORC_MUTANT == 13 ? q[IDX(i, k)] : conj(q[IDX(k, i)])) * x[IDX(k, j)];
+            pm[IDX(i, j)] = s;
+        }
     return 0;
 }
 

@@ -21,6 +21,12 @@ Workloads (sizes follow the paper's experiments and the accuracy targets):
 * :func:`kappa_controlled` -- the accuracy generator of Sec. 5.1:
   A = Q Lam Q^T / ||Lam||_F with kappa(A) = kappa, and B likewise.
 * :func:`uniform01` -- A, B uniform on [0, 1] (the speed generator of Sec. 5.1).
+* :func:`sign_case`, :func:`polar_case`, :func:`sylvester_case` -- the
+  "work backwards" generators of Sec. 5.3-5.5, whose answers are known by
+  construction: X = Z J Z^{-1} with sign(X) = Z sign(Re J) Z^{-1}; X = U P
+  with U from the QR factorization of a random matrix and P = Z^H Z; and
+  A = Z_A J_A Z_A^{-1}, B likewise (or B = A^H), C = A Y + Y B.  Entries of
+  Z, Y are uniform on [-1, 1] in real and imaginary part, as in the paper.
 """
 from __future__ import annotations
 
@@ -155,3 +161,64 @@ def kappa_controlled(n: int, kappa: float = 10.0, seed: int = 7) -> np.ndarray:
 def ulp_params() -> dict:
     """Unit roundoffs used by the tolerance derivations."""
     return {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def _unif_c(g: np.random.Generator, shape) -> np.ndarray:
+    re = g.uniform(-1.0, 1.0, shape)
+    im = g.uniform(-1.0, 1.0, shape)
+    return re + 1j * im
+
+
+def sign_case(n: int, seed: int = 21, re_lo: float = 0.5, re_hi: float = 1.5):
+    """X = Z J Z^{-1} and its sign Z diag(sign(Re J)) Z^{-1} (Sec. 5.3).
+
+    J is diagonal; its first ceil(n/2) entries have real part in [re_lo,
+    re_hi] and the rest in [-re_hi, -re_lo] (kept away from zero), imaginary
+    parts uniform on [-1, 1]; Z has real and imaginary parts uniform on
+    [-1, 1].  Returns (X, sign(X)), complex128."""
+    g = _rng(seed)
+    z = _unif_c(g, (n, n))
+    p = (n + 1) // 2
+    mag = g.uniform(re_lo, re_hi, n)
+    sgn = np.where(np.arange(n) < p, 1.0, -1.0)
+    j = sgn * mag + 1j * g.uniform(-1.0, 1.0, n)
+    zi = np.linalg.inv(z)
+    return (z * j) @ zi, (z * sgn) @ zi
+
+
+def polar_case(n: int, seed: int = 22):
+    """X = U P with U unitary (from the QR factorization of a matrix with
+    entries uniform on [-1, 1] in real and imaginary part) and P = Z^H Z for
+    a second such matrix Z (Sec. 5.5).  Returns (X, U, P), complex128."""
+    g = _rng(seed)
+    y = _unif_c(g, (n, n))
+    z = _unif_c(g, (n, n))
+    u, _ = np.linalg.qr(y)
+    p = z.conj().T @ z
+    return u @ p, u, p
+
+
+def sylvester_case(p: int, q: int, seed: int = 23, lyapunov: bool = False, re_lo: float = 9.0, re_hi: float = 10.0):
+    """A Y + Y B = C with known Y (Sec. 5.4): A = Z_A J_A Z_A^{-1} with J_A
+    diagonal, real parts uniform on [re_lo, re_hi] (so sign(A) = I) and
+    imaginary parts uniform on [-1, 1]; B the same way with its own Z_B and
+    J_B (or B = A^H when ``lyapunov``, which needs p == q); Y with entries
+    uniform on [-1, 1] in real and imaginary part; C = A Y + Y B.  Returns
+    (A, B, C, Y), complex128."""
+    g = _rng(seed)
+
+    def stable(k):
+        z = _unif_c(g, (k, k))
+        j = g.uniform(re_lo, re_hi, k) + 1j * g.uniform(-1.0, 1.0, k)
+        return (z * j) @ np.linalg.inv(z)
+
+    a = stable(p)
+    if lyapunov:
+        if p != q:
+            raise ValueError("the Lyapunov equation has p == q")
+        b = a.conj().T
+    else:
+        b = stable(q)
+    y = _unif_c(g, (p, q))
+    c = a @ y + y @ b
+    return a, b, c, y

@@ -25,6 +25,9 @@ MUTANTS = {
     8: "X^T instead of X^H in the adjoint",
     9: "X + X^{-1} instead of (X + X^{-1})/2 in the sign iteration",
     10: "y = y2 - y1 (the printed sign) in the Frobenius linear solve",
+    11: "X^{-1} instead of X^{-H} in the polar iteration",
+    12: "Y = +1/2 of the top-right block instead of -1/2 (Sylvester)",
+    13: "P = Q X instead of Q^H X (polar decomposition)",
 }
 
 
@@ -82,6 +85,15 @@ def _pin_failures(o) -> list:
     sref = z @ np.diag(np.sign(re)) @ np.linalg.inv(z)
     if np.abs(o.sign_newton(x, 40) - sref).max() > 1e-9 * np.abs(sref).max():
         fails.append("sign closed form")
+    # polar decomposition and Sylvester equation against their constructions
+    x, u, p = W.polar_case(5, seed=41)
+    qf, pf, _ = o.polar(x, 1e-13, 100)
+    if np.abs(qf - u).max() > 1e-9 or np.abs(pf - p).max() > 1e-9 * np.abs(p).max():
+        fails.append("polar closed form")
+    a, b, c, y = W.sylvester_case(4, 3, seed=51)
+    yf, _ = o.sylvester(a, b, c, 1e-13, 100)
+    if np.abs(yf - y).max() > 1e-9 * np.abs(y).max():
+        fails.append("sylvester closed form")
     # Frobenius linear solve against LAPACK
     m = g.standard_normal((9, 9)) + 1j * g.standard_normal((9, 9))
     rhs = g.standard_normal((9, 2)) + 1j * g.standard_normal((9, 2))
