@@ -221,6 +221,67 @@ def measure_batched(frob, dev, steps, rank):
     return out
 
 
+def measure_newton(frob, dev):
+    """The Newton drivers at the smallest sizes of the paper's experiments
+    (Sec. 5.3-5.5), FP64, with its stopping rules: the matrix sign of
+    X = Z J Z^{-1} (n = 2100, eps = 1e-3), the polar decomposition of X = U P
+    (n = 2100, eps = 1e-3) and the Sylvester equation with p = q = 1050
+    (eps = 1e-1); every inverse a Frobenius inversion or, as the baseline,
+    a complex-LU inversion.  Wall time of one driver call (CUDA events; the
+    driver reads a 4-byte count from the device after each step), steps, and
+    the relative forward error (max norm) against the answer the
+    construction fixes."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / np.abs(b).max())
+
+    def timed_call(f):
+        f()  # warm-up (workspace, first-use setup)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = f()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return r, e0.elapsed_time(e1)
+
+    out = {}
+    n = 2100
+    x, s = W.sign_case(n, seed=61)
+    dx = torch.from_numpy(x).to(dev)
+    res = {}
+    for route in ("frob", "cplx_lu"):
+        r, ms = timed_call(lambda: frob.sign(dx, route=route, eps=1e-3, kmax=100, check=False))
+        k = int(r.steps()[0])
+        res[route] = {"ms": ms, "steps": k, "ms_per_step": ms / max(k, 1),
+                      "forward_error": rel(r.out.cpu().numpy(), s)}
+    out["sign_n2100"] = res
+    x, u, pm = W.polar_case(n, seed=62)
+    dx = torch.from_numpy(x).to(dev)
+    res = {}
+    for route in ("frob", "cplx_lu"):
+        r, ms = timed_call(lambda: frob.polar(dx, route=route, eps=1e-3, kmax=100, check=False))
+        k = int(r.steps()[0])
+        q, p_ = (t.cpu().numpy() for t in r.out)
+        res[route] = {"ms": ms, "steps": k, "ms_per_step": ms / max(k, 1), "forward_error_q": rel(q, u),
+                      "forward_error_p": rel(p_, pm)}
+    out["polar_n2100"] = res
+    a, b, c, y = W.sylvester_case(1050, 1050, seed=63)
+    da, db, dc = (torch.from_numpy(t).to(dev) for t in (a, b, c))
+    res = {}
+    for route in ("frob", "cplx_lu"):
+        r, ms = timed_call(lambda: frob.sylvester(da, db, dc, route=route, eps=1e-1, kmax=100, check=False))
+        k = int(r.steps()[0])
+        res[route] = {"ms": ms, "steps": k, "ms_per_step": ms / max(k, 1),
+                      "forward_error": rel(r.out.cpu().numpy(), y)}
+    out["sylvester_p1050_q1050"] = res
+    return out
+
+
 def measure_solve(frob, dev, steps):
     """Linear systems (Sec. 5.2): 16 systems of order 512, one right-hand
     side, A and B from the kappa = 10 generator of Sec. 5.1 and x, y uniform
@@ -283,6 +344,7 @@ def main():
     ap.add_argument("--once-mixed", action="store_true",
                     help="as --once, for the mixed-precision form")
     ap.add_argument("--no-batched", action="store_true", help="skip the 1024-matrix uneven workload")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-driver workloads (sign, polar, Sylvester)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="matrices per step for --once / --once-mixed (profiling a smaller case)")
     args = ap.parse_args()
@@ -437,6 +499,7 @@ def main():
 
     batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
     solve = None if args.no_batched else measure_solve(frob, dev, 3)
+    newton = None if (args.no_newton or args.no_batched) else measure_newton(frob, dev)
 
     # end to end through the public API with host buffers
     def e2e_step():
@@ -488,6 +551,7 @@ def main():
         "mixed_tol_1e-15": mixed_fine,
         "batched_uneven": batched,
         "linear_solve": solve,
+        "newton_drivers": newton,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),

@@ -267,6 +267,55 @@ frob_status cplx_lu_solve(int n, int nrhs, int batch, const void* M, int64_t ldm
                           int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
                           frob_info* info, void* stream);
 
+/*
+ * Newton drivers over the batched inversions (Sec. 5.3-5.5), each step a
+ * Frobenius inversion of the whole batch (route FROB_ROUTE_FROB, any
+ * precision frob_inv accepts) or, as the baseline, a complex-LU inversion
+ * (FROB_ROUTE_CPLX_LU, FROB_FP64 or FROB_FP32).
+ *
+ * frob_newton -- X_0 = M and, for kind FROB_NEWTON_SIGN, the matrix sign
+ * iteration X_{k+1} = (X_k + X_k^{-1}) / 2 (Sec. 5.3, eq. "iter"); for
+ * FROB_NEWTON_POLAR, X_{k+1} = (X_k + X_k^{-H}) / 2 (Sec. 5.5, eq. "iter2"),
+ * whose limit is the unitary polar factor.  A matrix stops after the first
+ * step k with ||X_k - X_{k-1}||_max <= eps ||X_k||_max (max of the entries'
+ * moduli; the rule of Sec. 5.3) or after kmax steps; the call returns when
+ * every matrix of the batch has stopped, with X holding the last iterates and
+ * steps[b] (device, int32 per matrix) the steps matrix b took.  The host
+ * reads one 4-byte count after each step (a stream synchronisation), so the
+ * call is not graph-capturable.  M and X as for frob_inv (complex128, or
+ * complex64 for FROB_FP32; X may equal M exactly, other overlap is an
+ * error).  info[b] (device) is zero unless an inversion failed, in which case
+ * it is that inversion's record and matrix b stopped there.  opts as for
+ * frob_inv (the almost sure option is ignored).  Workspace:
+ * frob_newton_workspace_bytes(n, batch, prec, route).
+ *
+ * frob_sylvester -- Y with A Y + Y B = C (A p x p, B q x q, C and Y p x q;
+ * lyapunov = 1: B = A^H and the B argument is ignored) through the sign of
+ * [[A, -C], [0, -B]], which is [[I, -2Y], [0, -I]] when sign(A) = I and
+ * sign(B) = I (Sec. 5.4): the sign iteration above on the block matrix, then
+ * Y = -1/2 its top-right block.  Workspace:
+ * frob_sylvester_workspace_bytes(p, q, batch, prec, route).
+ *
+ * frob_polar -- X = Q P (Sec. 5.5): Q by the FROB_NEWTON_POLAR iteration from
+ * X, then P = Q^H X.  Q and P must not overlap X.  Workspace:
+ * frob_polar_workspace_bytes(n, batch, prec, route).
+ */
+typedef enum { FROB_NEWTON_SIGN = 0, FROB_NEWTON_POLAR = 1 } frob_newton_kind;
+typedef enum { FROB_ROUTE_FROB = 0, FROB_ROUTE_CPLX_LU = 1 } frob_inv_route;
+size_t frob_newton_workspace_bytes(int n, int batch, int prec, int route);
+frob_status frob_newton(int kind, int route, int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X,
+                        int64_t ldx, int64_t sx, const frob_opts* opts, double eps, int kmax, void* ws, size_t wsb,
+                        frob_info* info, int32_t* steps, void* stream);
+size_t frob_sylvester_workspace_bytes(int p, int q, int batch, int prec, int route);
+frob_status frob_sylvester(int route, int p, int q, int batch, const void* A, int64_t lda, int64_t sa, const void* B,
+                           int64_t ldb, int64_t sb, int lyapunov, const void* C, int64_t ldc, int64_t sc, void* Y,
+                           int64_t ldy, int64_t sy, const frob_opts* opts, double eps, int kmax, void* ws, size_t wsb,
+                           frob_info* info, int32_t* steps, void* stream);
+size_t frob_polar_workspace_bytes(int n, int batch, int prec, int route);
+frob_status frob_polar(int route, int n, int batch, const void* X, int64_t ldx, int64_t sx, void* Q, int64_t ldq,
+                       int64_t sq, void* P, int64_t ldp, int64_t sp, const frob_opts* opts, double eps, int kmax,
+                       void* ws, size_t wsb, frob_info* info, int32_t* steps, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 

@@ -114,6 +114,22 @@ def load() -> ctypes.CDLL:
         lib.frob_gemm_tc.restype = i32
         lib.frob_gemm_tc_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
         lib.frob_gemm_tc_workspace_bytes.restype = sz
+        lib.frob_newton_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        lib.frob_newton_workspace_bytes.restype = sz
+        lib.frob_polar_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        lib.frob_polar_workspace_bytes.restype = sz
+        lib.frob_sylvester_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
+        lib.frob_sylvester_workspace_bytes.restype = sz
+        dbl = ctypes.c_double
+        lib.frob_newton.argtypes = [i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, ctypes.POINTER(FrobOpts), dbl,
+                                    i32, vp, sz, vp, vp, vp]
+        lib.frob_newton.restype = i32
+        lib.frob_polar.argtypes = [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, ctypes.POINTER(FrobOpts),
+                                   dbl, i32, vp, sz, vp, vp, vp]
+        lib.frob_polar.restype = i32
+        lib.frob_sylvester.argtypes = [i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, i32, vp, i64, i64, vp, i64, i64,
+                                       ctypes.POINTER(FrobOpts), dbl, i32, vp, sz, vp, vp, vp]
+        lib.frob_sylvester.restype = i32
         lib.frob_profile_enable.argtypes = [i32]
         lib.frob_profile_enable.restype = None
         lib.frob_profile_report.argtypes = [ctypes.c_char_p, sz]
@@ -368,6 +384,142 @@ def frob_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bo
 def cplx_lu_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bool = True) -> Result:
     """Solve M X = RHS by complex LU with partial pivoting (baseline)."""
     return _solve("cplx_lu_solve", 1, m, rhs, prec, check)
+
+
+ROUTE = {"frob": 0, "cplx_lu": 1}
+
+
+class NewtonResult:
+    """Output of a Newton driver: the result tensor(s), the per-matrix step
+    counts and the device-side info records."""
+
+    def __init__(self, out, steps: torch.Tensor, info: torch.Tensor):
+        self.out = out
+        self.steps_dev = steps
+        self.info_dev = info
+
+    def steps(self) -> np.ndarray:
+        return self.steps_dev.cpu().numpy()
+
+    def info(self) -> np.ndarray:
+        return parse_info(self.info_dev)
+
+
+def _batch3(t: torch.Tensor, what: str, prec: str) -> torch.Tensor:
+    if t.dtype != _cdtype(prec) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA {_cdtype(prec)} tensor for prec={prec}")
+    t3 = t.unsqueeze(0) if t.dim() == 2 else t
+    if t3.dim() != 3:
+        raise ValueError(f"{what}: expected 2 or 3 dimensions, got {tuple(t.shape)}")
+    return t3 if t3.stride(-1) == 1 else t3.contiguous()
+
+
+def _ws(need: int, dev) -> tuple:
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    pad = (-ws.data_ptr()) % 256
+    return ws, ws.data_ptr() + pad, ws.numel() - pad
+
+
+def _newton_call(kind: int, m: torch.Tensor, prec: str, route: str, eps: float, kmax: int, check: bool, what: str,
+                 ns_tol: float = 1e-14) -> NewtonResult:
+    lib = load()
+    m3 = _batch3(m, what, prec)
+    batch, n = m3.shape[0], m3.shape[-1]
+    if m3.shape[-2] != n:
+        raise ValueError(f"{what}: expected square matrices")
+    x3 = torch.empty((batch, n, n), dtype=m3.dtype, device=m3.device)
+    need = int(lib.frob_newton_workspace_bytes(n, batch, PREC[prec], ROUTE[route]))
+    if need == 0:
+        raise FrobError(f"{what}: unsupported precision / route", FROB_ERR_UNSUPPORTED)
+    ws, wp, wb = _ws(need, m3.device)
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=m3.device)
+    steps = torch.zeros(batch, dtype=torch.int32, device=m3.device)
+    o = _opts(prec, ns_tol=ns_tol)
+    with torch.cuda.device(m3.device):
+        st = lib.frob_newton(kind, ROUTE[route], n, batch, m3.data_ptr(), m3.stride(1), m3.stride(0), x3.data_ptr(),
+                             x3.stride(1), x3.stride(0), ctypes.byref(o), float(eps), int(kmax), wp, wb,
+                             info.data_ptr(), steps.data_ptr(), torch.cuda.current_stream(m3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"{what}: {status_str(st)}", st)
+    res = NewtonResult(x3 if m.dim() == 3 else x3[0], steps, info)
+    if check:
+        check_info(res.info(), what)
+    return res
+
+
+def sign(m: torch.Tensor, prec: str = "fp64", route: str = "frob", eps: float = 1e-3, kmax: int = 100,
+         check: bool = True) -> NewtonResult:
+    """Matrix sign function by Newton's iteration X <- (X + X^{-1})/2 with
+    the stopping rule of Sec. 5.3 (relative change in the max norm <= eps,
+    at most kmax steps); every inverse a Frobenius inversion (route "frob")
+    or, as the baseline, a complex-LU inversion (route "cplx_lu")."""
+    return _newton_call(0, m, prec, route, eps, kmax, check, "sign")
+
+
+def polar(x: torch.Tensor, prec: str = "fp64", route: str = "frob", eps: float = 1e-3, kmax: int = 100,
+          check: bool = True) -> NewtonResult:
+    """Polar decomposition X = Q P (Sec. 5.5): Q by X <- (X + X^{-H})/2 with
+    the stopping rule of Sec. 5.3, P = Q^H X.  ``out`` is (Q, P)."""
+    lib = load()
+    x3 = _batch3(x, "polar", prec)
+    batch, n = x3.shape[0], x3.shape[-1]
+    q3 = torch.empty((batch, n, n), dtype=x3.dtype, device=x3.device)
+    p3 = torch.empty_like(q3)
+    need = int(lib.frob_polar_workspace_bytes(n, batch, PREC[prec], ROUTE[route]))
+    if need == 0:
+        raise FrobError("polar: unsupported precision / route", FROB_ERR_UNSUPPORTED)
+    ws, wp, wb = _ws(need, x3.device)
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=x3.device)
+    steps = torch.zeros(batch, dtype=torch.int32, device=x3.device)
+    o = _opts(prec)
+    with torch.cuda.device(x3.device):
+        st = lib.frob_polar(ROUTE[route], n, batch, x3.data_ptr(), x3.stride(1), x3.stride(0), q3.data_ptr(),
+                            q3.stride(1), q3.stride(0), p3.data_ptr(), p3.stride(1), p3.stride(0), ctypes.byref(o),
+                            float(eps), int(kmax), wp, wb, info.data_ptr(), steps.data_ptr(),
+                            torch.cuda.current_stream(x3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"polar: {status_str(st)}", st)
+    out = (q3, p3) if x.dim() == 3 else (q3[0], p3[0])
+    res = NewtonResult(out, steps, info)
+    if check:
+        check_info(res.info(), "polar")
+    return res
+
+
+def sylvester(a: torch.Tensor, b: torch.Tensor | None, c: torch.Tensor, prec: str = "fp64", route: str = "frob",
+              eps: float = 1e-1, kmax: int = 100, lyapunov: bool = False, check: bool = True) -> NewtonResult:
+    """Y with A Y + Y B = C (Sec. 5.4) from the sign of [[A, -C], [0, -B]];
+    ``lyapunov=True`` takes B = A^H (b is ignored).  ``out`` is Y."""
+    lib = load()
+    a3 = _batch3(a, "sylvester", prec)
+    c3 = _batch3(c, "sylvester", prec)
+    batch, p, q = a3.shape[0], a3.shape[-1], c3.shape[-1]
+    if lyapunov:
+        b3 = a3
+    else:
+        b3 = _batch3(b, "sylvester", prec)
+    if c3.shape[0] != batch or c3.shape[-2] != p or b3.shape[-1] != q:
+        raise ValueError("sylvester: A (p, p), B (q, q), C (p, q)")
+    y3 = torch.empty((batch, p, q), dtype=a3.dtype, device=a3.device)
+    need = int(lib.frob_sylvester_workspace_bytes(p, q, batch, PREC[prec], ROUTE[route]))
+    if need == 0:
+        raise FrobError("sylvester: unsupported precision / route", FROB_ERR_UNSUPPORTED)
+    ws, wp, wb = _ws(need, a3.device)
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=a3.device)
+    steps = torch.zeros(batch, dtype=torch.int32, device=a3.device)
+    o = _opts(prec)
+    with torch.cuda.device(a3.device):
+        st = lib.frob_sylvester(ROUTE[route], p, q, batch, a3.data_ptr(), a3.stride(1), a3.stride(0), b3.data_ptr(),
+                                b3.stride(1), b3.stride(0), 1 if lyapunov else 0, c3.data_ptr(), c3.stride(1),
+                                c3.stride(0), y3.data_ptr(), y3.stride(1), y3.stride(0), ctypes.byref(o), float(eps),
+                                int(kmax), wp, wb, info.data_ptr(), steps.data_ptr(),
+                                torch.cuda.current_stream(a3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"sylvester: {status_str(st)}", st)
+    res = NewtonResult(y3 if a.dim() == 3 else y3[0], steps, info)
+    if check:
+        check_info(res.info(), "sylvester")
+    return res
 
 
 def inv_adjoint(x: torch.Tensor, g: torch.Tensor, prec: str | None = None) -> torch.Tensor:
