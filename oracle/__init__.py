@@ -17,6 +17,8 @@ of Dai, Lim and Ye, "Complex matrix inversion via real matrix inversions":
 * :func:`frob_inv_basic` -- Algorithm "Frobenius inversion" with tau = 1
                            (Sec. 2, Lemma 2.3): two explicit real inversions,
                            three products, one addition.
+* :func:`frob_inv_b`    -- the formula for invertible B (Sec. 4.2, before
+                           Lemma "rand Frob"), explicit real inversions.
 * :func:`frob_inv_lu`   -- Algorithm "Frobenius inversion with LU
                            decomposition" (Sec. 4.1).
 * :func:`frob_inv_rand` -- Algorithm "Almost sure Frobenius inversion"
@@ -120,6 +122,7 @@ class Oracle:
             "orc_cplx_chol_inv": [i, zp, zp],
             "orc_frob_inv_basic": [i, zp, zp, zp, zp, zp],
             "orc_frob_inv_lu": [i, zp, zp],
+            "orc_frob_inv_b": [i, zp, zp],
             "orc_frob_inv_rand": [i, zp, ctypes.c_double, zp],
             "orc_frob_inv_chol": [i, zp, zp],
             "orc_inv2x2": [zp, zp],
@@ -165,6 +168,14 @@ class Oracle:
         _check("frob_inv_basic",
                self.lib.orc_frob_inv_basic(n, _ptr(m), _ptr(x), _ptr(x2), _ptr(s), _ptr(sinv)))
         return (x, (x2, s, sinv)) if stages else x
+
+    def frob_inv_b(self, m) -> np.ndarray:
+        """The formula for invertible B (Sec. 4.2): B^{-1}A(AB^{-1}A + B)^{-1}
+        - i(AB^{-1}A + B)^{-1}, explicit real inversions."""
+        m, n = _prep(m)
+        x = np.empty_like(m)
+        _check("frob_inv_b", self.lib.orc_frob_inv_b(n, _ptr(m), _ptr(x)))
+        return x
 
     def frob_inv_lu(self, m) -> np.ndarray:
         m, n = _prep(m)
@@ -290,6 +301,10 @@ def cplx_chol_inv(m):
 
 def frob_inv_basic(m, stages: bool = False):
     return load().frob_inv_basic(m, stages)
+
+
+def frob_inv_b(m):
+    return load().frob_inv_b(m)
 
 
 def frob_inv_lu(m):

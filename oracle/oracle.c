@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORC_MUTANT plants one deliberate mistake (k = 1..13) so that a test can check
+/* ORC_MUTANT plants one deliberate mistake (k = 1..14) so that a test can check
  * that the pins catch it.  Product builds of the oracle use ORC_MUTANT = 0. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -341,6 +341,33 @@ int orc_frob_inv_basic(int n, const zc *m, zc *x, double *x2_out, double *s_out,
     if (x2_out) memcpy(x2_out, X2, sizeof(double) * nn);
     if (s_out) memcpy(s_out, X4, sizeof(double) * nn);
     if (sinv_out) memcpy(sinv_out, X5, sizeof(double) * nn);
+    free(w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The formula for invertible B (Sec. 4.2, before Lemma "rand Frob"):         */
+/* (A + iB)^{-1} = B^{-1} A (A B^{-1} A + B)^{-1} - i (A B^{-1} A + B)^{-1}.  */
+/* Y1 = B^{-1}; Y2 = Y1 A; T = B + A Y2; Y5 = T^{-1}; Y6 = Y2 Y5;             */
+/* result Y6 - i Y5.  Explicit real inversions, as written.                   */
+/* ------------------------------------------------------------------------- */
+int orc_frob_inv_b(int n, const zc *m, zc *x)
+{
+    if (n < 1) return -2;
+    size_t nn = (size_t)n * n;
+    double *w = malloc(sizeof(double) * nn * 7);
+    if (!w) return -1;
+    double *A = w, *B = w + nn, *Y1 = w + 2 * nn, *Y2 = w + 3 * nn, *T = w + 4 * nn, *Y5 = w + 5 * nn,
+           *Y6 = w + 6 * nn;
+    split_planes(n, m, A, B);
+    int info = dinv_plain(n, B, Y1);
+    if (info) { free(w); return info; }
+    dgemm_plain(n, Y1, A, NULL, Y2);   /* Y2 = B^{-1} A          */
+    dgemm_plain(n, A, Y2, B, T);       /* T = B + A B^{-1} A     */
+    info = dinv_plain(n, T, Y5);       /* Y5 = T^{-1}            */
+    if (info) { free(w); return info; }
+    dgemm_plain(n, Y2, Y5, NULL, Y6);  /* Y6 = B^{-1} A T^{-1}   */
+    for (size_t t = 0; t < nn; ++t) x[t] = Y6[t] - (ORC_MUTANT == 14 ? -1.0 : 1.0) * I * Y5[t];
     free(w);
     return 0;
 }

@@ -28,6 +28,7 @@ MUTANTS = {
     11: "X^{-1} instead of X^{-H} in the polar iteration",
     12: "Y = +1/2 of the top-right block instead of -1/2 (Sylvester)",
     13: "P = Q X instead of Q^H X (polar decomposition)",
+    14: "Y6 + i Y5 instead of Y6 - i Y5 (formula for invertible B)",
 }
 
 
@@ -44,6 +45,7 @@ def _pin_failures(o) -> list:
             "basic": lambda: o.frob_inv_basic(m),
             "lu": lambda: o.frob_inv_lu(m),
             "rand": lambda: o.frob_inv_rand(m, 0.37),
+            "b": lambda: o.frob_inv_b(m),
         }
         for name, f in routes.items():
             try:

@@ -305,3 +305,36 @@ def test_ill_conditioned_generator():
     assert abs(np.linalg.cond(m.imag) - 1) < 1e-8
     kappa = np.linalg.cond(m)
     assert 1e5 < kappa < 1e7
+
+
+# ------------------------------------------------------------------ formula for invertible B (Sec. 4.2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_frob_inv_b_adjugate(oracle_lib, n):
+    g = np.random.default_rng(700 + n)
+    m = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    assert metrics.forward_error(oracle.frob_inv_b(m), oracle.adjugate_inv(m)) <= 1e-12
+
+
+def test_frob_inv_b_singular_real_part(oracle_lib):
+    """A singular, B invertible: the A route fails at its last pivot, the B
+    formula gives the inverse (LAPACK on the unique result)."""
+    g = np.random.default_rng(71)
+    n = 30
+    a = g.standard_normal((n, n))
+    a[:, 7] = 0.0
+    m = a + 1j * g.standard_normal((n, n))
+    with pytest.raises(oracle.OracleError):
+        oracle.frob_inv_lu(m)
+    assert metrics.forward_error(oracle.frob_inv_b(m), np.linalg.inv(m)) <= 1e-11
+
+
+def test_frob_inv_b_is_frobenius_of_minus_i_m(oracle_lib):
+    """(A + iB)^{-1} = -i (B - iA)^{-1}: the B formula equals -i times the A
+    formula applied to B - iA."""
+    g = np.random.default_rng(72)
+    m = g.standard_normal((9, 9)) + 1j * g.standard_normal((9, 9))
+    mp = m.imag - 1j * m.real
+    assert np.abs(oracle.frob_inv_b(m) - (-1j) * oracle.frob_inv_basic(mp)).max() <= 1e-12 * np.abs(
+        np.linalg.inv(m)).max()
