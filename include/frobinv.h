@@ -86,7 +86,21 @@ typedef struct {
                           "rand Frob": at most n values of mu fail) */
   int32_t ns_max_iter; /* mixed modes: refinement iteration limit */
   double ns_tol;       /* mixed modes: target ||I - M X||_F/(||M||_F ||X||_F) */
-} frob_opts;           /* NULL => {FROB_FP64, 0, 0, 0, 8, 1e-14} */
+  int32_t part;        /* frob_inv only: which real part is factored (frob_part).
+                          FROB_PART_A: eq. "Finv", A invertible.
+                          FROB_PART_B: the formula for invertible B (Sec. 4.2),
+                          (A + iB)^{-1} = B^{-1}A(AB^{-1}A + B)^{-1}
+                          - i(AB^{-1}A + B)^{-1}, computed as the A route on
+                          -iM = B - iA followed by a multiplication by -i.
+                          FROB_PART_AUTO: per matrix, both A and B are
+                          factored (one extra LU, 2n^3/3 flops) and the one
+                          whose U has the larger min |u_kk| / max |u_kk| is
+                          used (a singular factor counts as 0).  Not with
+                          almost_sure. */
+  int32_t reserved;    /* must be 0 */
+} frob_opts;           /* NULL => {FROB_FP64, 0, 0, 0, 8, 1e-14, FROB_PART_A, 0} */
+
+typedef enum { FROB_PART_A = 0, FROB_PART_B = 1, FROB_PART_AUTO = 2 } frob_part;
 
 typedef struct {
   int32_t status;    /* frob_status of this matrix */

@@ -234,6 +234,8 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
                      const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
   frob_opts o = opts ? *opts : default_opts();
   if (o.almost_sure != 0 && o.almost_sure != 1) return FROB_ERR_ARG;
+  if (o.part < FROB_PART_A || o.part > FROB_PART_AUTO || o.reserved != 0) return FROB_ERR_ARG;
+  if (o.part != FROB_PART_A && o.almost_sure) return FROB_ERR_ARG;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_INV, n, batch, o.prec), info, o.prec);
   if (s != FROB_OK) return s;

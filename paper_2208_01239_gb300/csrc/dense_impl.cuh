@@ -187,6 +187,7 @@ template <typename R> struct EpiFrobOut {
   const int* rp;     // per-matrix permutation, batch stride n, or NULL
   int n;
   const frob_info* info; // info[b].mu, or NULL for mu = 0
+  const int* partb = nullptr;  // partb[b] = 1: the inverse of -iM was formed, M^{-1} = -i (X3 + i X4)
   __device__ __forceinline__ void operator()(int b, int i, int j, R w) const {
     R x3 = Z.at(b)[(int64_t)i * Z.ld + j];
     R x4 = -w;
@@ -196,6 +197,9 @@ template <typename R> struct EpiFrobOut {
       R mu = (R)info[b].mu;
       out.x = x3 - mu * x4;
       out.y = mu * x3 + x4;
+    } else if (partb && partb[b]) {
+      out.x = x4;
+      out.y = -x3;
     } else {
       out.x = x3;
       out.y = x4;

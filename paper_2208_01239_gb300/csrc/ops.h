@@ -17,6 +17,8 @@ template <> struct cplx_of<float> { using type = zf; };
 template <typename R> struct Planes {
   MatB<R> LA, S, Bp, X1, Y;
   int *piv1, *piv2, *rp1, *rp2;
+  int* partb;         // [batch] 1: B factored (frob_lu_run)
+  frob_info* infoB;   // [batch] status of the LU of B (FROB_PART_AUTO)
 };
 // Workspace of the complex baselines.
 template <typename C> struct CPlanes {

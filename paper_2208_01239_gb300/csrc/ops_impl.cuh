@@ -43,16 +43,24 @@ __device__ __forceinline__ void init_info(frob_info* info, int b, double mu) {
 // M = A + iB (interleaved) -> planes A (two copies: one is factorised, one
 // becomes S) and B.  Almost sure variant (Sec. 4.2): A' = A - mu B,
 // B' = mu A + B.  HPD variant (Sec. 4.3): only the lower triangle is read;
-// A = Re (symmetric), B = Im (skew-symmetric, zero diagonal).
+// A = Re (symmetric), B = Im (skew-symmetric, zero diagonal).  part = 1 (the
+// formula for invertible B): the planes of -iM = B - iA, A' = B, B' = -A.
+// LBc (FROB_PART_AUTO; p == NULL otherwise) receives a copy of B to factor.
 template <typename R>
 __global__ void split_kernel(int n, MatB<const typename cplx_of<R>::type> M, MatB<R> A1, MatB<R> A2, MatB<R> Bp,
-                             frob_info* info, int hpd, int almost_sure, uint64_t seed, int attempt) {
+                             frob_info* info, int hpd, int almost_sure, uint64_t seed, int attempt, int part = 0,
+                             MatB<R> LBc = MatB<R>{nullptr, 0, 0}, int* partb = nullptr,
+                             frob_info* infoB = nullptr) {
   const int b = blockIdx.z;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)n * n) return;
   const int i = (int)(e / n), j = (int)(e % n);
   const double mu = almost_sure ? draw_mu(seed, b, attempt) : 0.0;
-  if (e == 0) init_info(info, b, mu);
+  if (e == 0) {
+    init_info(info, b, mu);
+    if (infoB) init_info(infoB, b, 0.0);
+    if (partb) partb[b] = part == 1 ? 1 : 0;
+  }
   const auto* Mb = M.at(b);
   R a, bb;
   if (hpd) {
@@ -74,7 +82,12 @@ __global__ void split_kernel(int n, MatB<const typename cplx_of<R>::type> M, Mat
       R a2 = a - m * bb;
       bb = m * a + bb;
       a = a2;
+    } else if (part == 1) {
+      const R a2 = bb;
+      bb = -a;
+      a = a2;
     }
+    if (LBc.p) LBc.at(b)[(int64_t)i * LBc.ld + j] = bb;
   }
   A1.at(b)[(int64_t)i * A1.ld + j] = a;
   if (A2.p) A2.at(b)[(int64_t)i * A2.ld + j] = a;
@@ -360,8 +373,76 @@ size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.piv2 = c.take<int>((size_t)n * batch);
   p.rp1 = c.take<int>((size_t)n * batch);
   p.rp2 = c.take<int>((size_t)n * batch);
+  p.partb = c.take<int>((size_t)batch);
+  p.infoB = c.take<frob_info>((size_t)batch);
   if (out) *out = p;
   return c.off;
+}
+
+// FROB_PART_AUTO: per matrix, the pivot ratios min |u_kk| / max |u_kk| of
+// the LU factors of A (LA) and B (LB) (0 for a factorization that reported a
+// zero or non-finite pivot); B is chosen when its ratio is larger.  One CTA
+// per matrix.
+template <typename R>
+__global__ void choose_part_kernel(int n, MatB<const R> LA, MatB<const R> LB, const frob_info* info,
+                                   const frob_info* infoB, int* partb) {
+  const int b = blockIdx.x;
+  __shared__ double red[4][32];
+  double mina = INFINITY, maxa = 0.0, minb = INFINITY, maxb = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double ua = fabs((double)LA.at(b)[(int64_t)k * LA.ld + k]);
+    const double ub = fabs((double)LB.at(b)[(int64_t)k * LB.ld + k]);
+    mina = fmin(mina, ua);
+    maxa = fmax(maxa, ua);
+    minb = fmin(minb, ub);
+    maxb = fmax(maxb, ub);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mina = fmin(mina, __shfl_xor_sync(0xffffffffu, mina, o));
+    maxa = fmax(maxa, __shfl_xor_sync(0xffffffffu, maxa, o));
+    minb = fmin(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+    maxb = fmax(maxb, __shfl_xor_sync(0xffffffffu, maxb, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = mina;
+    red[1][w] = maxa;
+    red[2][w] = minb;
+    red[3][w] = maxb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      mina = fmin(mina, red[0][k]);
+      maxa = fmax(maxa, red[1][k]);
+      minb = fmin(minb, red[2][k]);
+      maxb = fmax(maxb, red[3][k]);
+    }
+    const double ra = (info[b].status == FROB_OK && maxa > 0.0 && maxa < INFINITY) ? mina / maxa : 0.0;
+    const double rb = (infoB[b].status == FROB_OK && maxb > 0.0 && maxb < INFINITY) ? minb / maxb : 0.0;
+    partb[b] = rb > ra ? 1 : 0;
+  }
+}
+
+// For the matrices that take B: LA <- LU of B, piv1 <- its pivots, and the
+// planes of -iM = B - iA: S <- B, Bp <- -A (S and Bp held A and B); the LU
+// of A's report, if any, is withdrawn.
+template <typename R>
+__global__ void swap_part_kernel(int n, const int* partb, MatB<R> LA, MatB<const R> LB, MatB<R> S, MatB<R> Bp,
+                                 int* piv1, const int* pivB, frob_info* info) {
+  const int b = blockIdx.z;
+  if (!partb[b]) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  LA.at(b)[(int64_t)i * LA.ld + j] = LB.at(b)[(int64_t)i * LB.ld + j];
+  R* ps = S.at(b) + (int64_t)i * S.ld + j;
+  R* pb = Bp.at(b) + (int64_t)i * Bp.ld + j;
+  const R a = *ps, bb = *pb;
+  *ps = bb;
+  *pb = -a;
+  if (j == 0) piv1[(int64_t)b * n + i] = pivB[(int64_t)b * n + i];
+  if (e == 0) init_info(info, b, 0.0);
 }
 
 template <typename R>
@@ -370,9 +451,21 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
   Planes<R> p;
   frob_lu_ws<R>(n, batch, ws, &p);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  const bool autop = o.part == FROB_PART_AUTO;
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
-                                                       o.attempt));
+                                                       o.attempt, o.part == FROB_PART_B ? 1 : 0,
+                                                       autop ? p.X1 : MatB<R>{nullptr, 0, 0}, p.partb,
+                                                       autop ? p.infoB : nullptr));
   getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                       // A = P1^T L1 U1
+  if (autop) {
+    // the LU of B in the X1 plane (free until the first solve), its pivots
+    // in rp1 (free until the row map is built); keep the better-conditioned
+    getrf<R>(n, batch, p.X1, p.rp1, p.infoB, 0, st);
+    FROB_LAUNCH("choose_part", st,
+                choose_part_kernel<R><<<batch, 256, 0, st>>>(n, cst(p.LA), cst(p.X1), info, p.infoB, p.partb));
+    FROB_LAUNCH("swap_part", st, swap_part_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(
+                                     n, p.partb, p.LA, cst(p.X1), p.S, p.Bp, p.piv1, p.rp1, info));
+  }
   rowperm(n, batch, p.piv1, p.rp1, st);
   trsm<R, OP_N, true, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);   // L1 Y = P1 B
   trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st); // U1 X1 = Y
@@ -382,7 +475,8 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
   rowperm(n, batch, p.piv2, p.rp2, st);
   trtri<R, true>(n, batch, cst(p.S), p.Y, p.LA, st);                                     // Y = L2^{-1}
   trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
-  EpiFrobOut<R> epi{X, cst(p.Y), p.rp2, n, o.almost_sure ? info : nullptr};
+  EpiFrobOut<R> epi{X, cst(p.Y), p.rp2, n, o.almost_sure ? info : nullptr,
+                    o.part != FROB_PART_A ? p.partb : nullptr};
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.X1), cst(p.Y), epi, 0, st);          // X = Z P2 - i X1 Z P2
 }
 
