@@ -282,6 +282,52 @@ def measure_newton(frob, dev):
     return out
 
 
+def measure_accuracy(frob, dev):
+    """The accuracy experiments of Sec. 5.1, 5.2 and 5.6 at kappa = 10, FP64:
+    left and right relative residuals in the paper's max norm (eq. "backerr":
+    ||Y X - I||_max / (||X||_max ||Y||_max), ||A + iB||_max = max(max|a_ij|,
+    max|b_ij|)) of Frobenius inversion against complex LU (general matrices,
+    the kappa-controlled generator) and against complex Cholesky (HPD,
+    kappa(X) = 10); and relative forward errors of linear solves (x, y
+    uniform on [-1, 1], c + id = M (x + iy)) by Frobenius, complex LU and
+    the 2n real augmented system.  Residuals computed on the host in FP64."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+
+    def mx(a):
+        return max(float(np.abs(a.real).max()), float(np.abs(a.imag).max()))
+
+    def res(x, y):
+        i = np.eye(x.shape[0])
+        return mx(y @ x - i) / (mx(x) * mx(y)), mx(x @ y - i) / (mx(x) * mx(y))
+
+    out = {"kappa": 10.0, "norm": "max of |Re|, |Im| entries (eq. maxnorm)"}
+    g = np.random.default_rng(13)
+    for n in (64, 512, 2048):
+        m = W.kappa_controlled(n, 10.0, seed=80 + n)
+        dm = torch.from_numpy(m).to(dev)
+        row = {}
+        for name, f in (("frob_inv", frob.frob_inv), ("cplx_lu_inv", frob.cplx_lu_inv)):
+            y = f(dm, check=False).x.cpu().numpy()
+            rl, rr = res(m, y)
+            row[name] = {"res_L": rl, "res_R": rr}
+        h = W.hpd_kappa(n, 10.0, seed=90 + n)
+        dh = torch.from_numpy(h).to(dev)
+        for name, f in (("frob_inv_hpd", frob.frob_inv_hpd), ("cplx_chol_inv", frob.cplx_chol_inv)):
+            y = f(dh, check=False).x.cpu().numpy()
+            rl, rr = res(h, y)
+            row[name] = {"res_L": rl, "res_R": rr}
+        xt = g.uniform(-1, 1, (n, 1)) + 1j * g.uniform(-1, 1, (n, 1))
+        rhs = torch.from_numpy(m @ xt).to(dev)
+        for name, f in (("frob_solve", frob.frob_solve), ("cplx_lu_solve", frob.cplx_lu_solve),
+                        ("aug_real_solve", frob.aug_real_solve)):
+            x = f(dm, rhs, check=False).x.cpu().numpy()
+            row[name] = {"forward_error": float(np.abs(x - xt).max() / np.abs(xt).max())}
+        out[f"n{n}"] = row
+    return out
+
+
 def measure_solve(frob, dev, steps):
     """Linear systems (Sec. 5.2): 16 systems of order 512, one right-hand
     side, A and B from the kappa = 10 generator of Sec. 5.1 and x, y uniform
@@ -345,6 +391,7 @@ def main():
                     help="as --once, for the mixed-precision form")
     ap.add_argument("--no-batched", action="store_true", help="skip the 1024-matrix uneven workload")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-driver workloads (sign, polar, Sylvester)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the kappa = 10 accuracy study")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="matrices per step for --once / --once-mixed (profiling a smaller case)")
     args = ap.parse_args()
@@ -500,6 +547,7 @@ def main():
     batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
     solve = None if args.no_batched else measure_solve(frob, dev, 3)
     newton = None if (args.no_newton or args.no_batched) else measure_newton(frob, dev)
+    accuracy = None if (args.no_accuracy or args.no_batched) else measure_accuracy(frob, dev)
 
     # end to end through the public API with host buffers
     def e2e_step():
@@ -552,6 +600,7 @@ def main():
         "batched_uneven": batched,
         "linear_solve": solve,
         "newton_drivers": newton,
+        "accuracy_kappa10": accuracy,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),

@@ -272,6 +272,11 @@ frob_status frob_inv_batched(int op, int batch, const int32_t* n_host, const int
  *
  * cplx_lu_solve -- the baseline: M = P^T L U in complex arithmetic, then
  * L U X = P B.  Workspace: frob_solve_workspace_bytes(1, ...).
+ *
+ * aug_real_solve -- the third method of Sec. 5.2: the 2n real augmented
+ * system [[A, -B], [B, A]] [x; y] = [c; d], by real LU with partial pivoting
+ * of the 2n x 2n matrix (bad_index up to 2n).  Workspace:
+ * frob_solve_workspace_bytes(2, ...).
  */
 size_t frob_solve_workspace_bytes(int op, int n, int nrhs, int batch, int prec);
 frob_status frob_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B, int64_t ldb,
@@ -280,6 +285,9 @@ frob_status frob_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, i
 frob_status cplx_lu_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B,
                           int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
                           frob_info* info, void* stream);
+frob_status aug_real_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B,
+                           int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
+                           frob_info* info, void* stream);
 
 /*
  * Newton drivers over the batched inversions (Sec. 5.3-5.5), each step a

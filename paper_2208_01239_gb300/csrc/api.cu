@@ -369,6 +369,7 @@ size_t frob_solve_workspace_bytes(int op, int n, int nrhs, int batch, int prec) 
   if (op == 0) return f32 ? frob_solve_ws<float>(n, nrhs, batch, nullptr, nullptr)
                           : frob_solve_ws<double>(n, nrhs, batch, nullptr, nullptr);
   if (op == 1) return f32 ? cplx_solve_ws<zf>(n, nrhs, batch) : cplx_solve_ws<zd>(n, nrhs, batch);
+  if (op == 2) return f32 ? aug_solve_ws<float>(n, nrhs, batch) : aug_solve_ws<double>(n, nrhs, batch);
   return 0;
 }
 
@@ -398,6 +399,13 @@ static frob_status solve_common(int op, int n, int nrhs, int batch, const void* 
     else
       frob_solve_run<double>(n, nrhs, batch, in_view<zd>(M, ldm, sm), in_view<zd>(B, ldb, sb),
                              out_view<zd>(X, ldx, sx), ws, info, st);
+  } else if (op == 2) {
+    if (prec == FROB_FP32)
+      aug_solve_run<float>(n, nrhs, batch, in_view<zf>(M, ldm, sm), in_view<zf>(B, ldb, sb), out_view<zf>(X, ldx, sx),
+                           ws, info, st);
+    else
+      aug_solve_run<double>(n, nrhs, batch, in_view<zd>(M, ldm, sm), in_view<zd>(B, ldb, sb),
+                            out_view<zd>(X, ldx, sx), ws, info, st);
   } else {
     if (prec == FROB_FP32)
       cplx_solve_run<zf>(n, nrhs, batch, in_view<zf>(M, ldm, sm), in_view<zf>(B, ldb, sb), out_view<zf>(X, ldx, sx),
@@ -419,6 +427,12 @@ frob_status cplx_lu_solve(int n, int nrhs, int batch, const void* M, int64_t ldm
                           int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
                           frob_info* info, void* stream) {
   return solve_common(1, n, nrhs, batch, M, ldm, sm, B, ldb, sb, X, ldx, sx, prec, ws, wsb, info, stream);
+}
+
+frob_status aug_real_solve(int n, int nrhs, int batch, const void* M, int64_t ldm, int64_t sm, const void* B,
+                           int64_t ldb, int64_t sb, void* X, int64_t ldx, int64_t sx, int prec, void* ws, size_t wsb,
+                           frob_info* info, void* stream) {
+  return solve_common(2, n, nrhs, batch, M, ldm, sm, B, ldb, sb, X, ldx, sx, prec, ws, wsb, info, stream);
 }
 
 const char* frob_status_str(int status) {

@@ -11,4 +11,7 @@ template void adjoint_run<float>(int, int, MatB<const zf>, MatB<const zf>, MatB<
 template size_t frob_solve_ws<float>(int, int, int, SolvePlanes<float>*, void*);
 template void frob_solve_run<float>(int, int, int, MatB<const zf>, MatB<const zf>, MatB<zf>, void*, frob_info*,
                                   cudaStream_t);
+template size_t aug_solve_ws<float>(int, int, int);
+template void aug_solve_run<float>(int, int, int, MatB<const zf>, MatB<const zf>, MatB<zf>, void*, frob_info*,
+                                 cudaStream_t);
 }  // namespace frob

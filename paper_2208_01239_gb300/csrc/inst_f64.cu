@@ -11,4 +11,7 @@ template void adjoint_run<double>(int, int, MatB<const zd>, MatB<const zd>, MatB
 template size_t frob_solve_ws<double>(int, int, int, SolvePlanes<double>*, void*);
 template void frob_solve_run<double>(int, int, int, MatB<const zd>, MatB<const zd>, MatB<zd>, void*, frob_info*,
                                   cudaStream_t);
+template size_t aug_solve_ws<double>(int, int, int);
+template void aug_solve_run<double>(int, int, int, MatB<const zd>, MatB<const zd>, MatB<zd>, void*, frob_info*,
+                                 cudaStream_t);
 }  // namespace frob

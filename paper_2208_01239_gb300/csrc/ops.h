@@ -48,6 +48,11 @@ void frob_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::
                     MatB<const typename cplx_of<R>::type> Bc, MatB<typename cplx_of<R>::type> X, void* ws,
                     frob_info* info, cudaStream_t st);
 template <typename C> size_t cplx_solve_ws(int n, int nrhs, int batch);
+template <typename R> size_t aug_solve_ws(int n, int nrhs, int batch);
+template <typename R>
+void aug_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::type> M,
+                   MatB<const typename cplx_of<R>::type> Bc, MatB<typename cplx_of<R>::type> X, void* ws,
+                   frob_info* info, cudaStream_t st);
 template <typename C>
 void cplx_solve_run(int n, int nrhs, int batch, MatB<const C> M, MatB<const C> Bc, MatB<C> X, void* ws,
                     frob_info* info, cudaStream_t st);

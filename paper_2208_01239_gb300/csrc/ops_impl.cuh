@@ -696,6 +696,81 @@ void cplx_solve_run(int n, int nrhs, int batch, MatB<const C> M, MatB<const C> B
   trsm<C, OP_N, false, false, false>(n, nrhs, batch, cst(W), cst(Y), X, nullptr, st);
 }
 
+// The 2n real augmented system (the third linear-solve method of Sec. 5.2):
+// [[A, -B], [B, A]] [x; y] = [c; d] for M (x + iy) = c + id, by real LU with
+// partial pivoting of the 2n x 2n matrix.  A failed pivot k (1-based, up to
+// 2n) is reported as FROB_ERR_SINGULAR with bad_index = k.
+template <typename R>
+__global__ void aug_build_kernel(int n, MatB<const typename cplx_of<R>::type> M, MatB<R> W) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const auto v = M.at(b)[(int64_t)i * M.ld + j];
+  R* w = W.at(b);
+  w[(int64_t)i * W.ld + j] = v.x;              // A
+  w[(int64_t)i * W.ld + n + j] = -v.y;         // -B
+  w[(int64_t)(n + i) * W.ld + j] = v.y;        // B
+  w[(int64_t)(n + i) * W.ld + n + j] = v.x;    // A
+}
+
+template <typename R>
+__global__ void aug_rhs_kernel(int n, int nrhs, MatB<const typename cplx_of<R>::type> Bc, MatB<R> CD,
+                               frob_info* info) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) init_info(info, b, 0.0);
+  if (e >= (int64_t)n * nrhs) return;
+  const int i = (int)(e / nrhs), j = (int)(e % nrhs);
+  const auto v = Bc.at(b)[(int64_t)i * Bc.ld + j];
+  CD.at(b)[(int64_t)i * CD.ld + j] = v.x;
+  CD.at(b)[(int64_t)(n + i) * CD.ld + j] = v.y;
+}
+
+template <typename R>
+__global__ void aug_out_kernel(int n, int nrhs, MatB<const R> XY, MatB<typename cplx_of<R>::type> X) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * nrhs) return;
+  const int i = (int)(e / nrhs), j = (int)(e % nrhs);
+  typename cplx_of<R>::type v;
+  v.x = XY.at(b)[(int64_t)i * XY.ld + j];
+  v.y = XY.at(b)[(int64_t)(n + i) * XY.ld + j];
+  X.at(b)[(int64_t)i * X.ld + j] = v;
+}
+
+template <typename R> size_t aug_solve_ws(int n, int nrhs, int batch) {
+  Carve c{nullptr};
+  plane<R>(c, 2 * n, batch);
+  c.take<R>((size_t)2 * n * nrhs * batch);
+  c.take<R>((size_t)2 * n * nrhs * batch);
+  c.take<int>((size_t)2 * n * batch);
+  c.take<int>((size_t)2 * n * batch);
+  return c.off;
+}
+
+template <typename R>
+void aug_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::type> M,
+                   MatB<const typename cplx_of<R>::type> Bc, MatB<typename cplx_of<R>::type> X, void* ws,
+                   frob_info* info, cudaStream_t st) {
+  Carve c{static_cast<unsigned char*>(ws)};
+  const int n2 = 2 * n;
+  MatB<R> W = plane<R>(c, n2, batch);
+  R* cdp = c.take<R>((size_t)n2 * nrhs * batch);
+  R* xyp = c.take<R>((size_t)n2 * nrhs * batch);
+  int* piv = c.take<int>((size_t)n2 * batch);
+  int* rp = c.take<int>((size_t)n2 * batch);
+  MatB<R> CD{cdp, nrhs, (int64_t)n2 * nrhs}, XY{xyp, nrhs, (int64_t)n2 * nrhs};
+  auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
+  FROB_LAUNCH("aug_build", st, aug_build_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, W));
+  FROB_LAUNCH("aug_rhs", st, aug_rhs_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, Bc, CD, info));
+  getrf<R>(n2, batch, W, piv, info, 0, st);
+  rowperm(n2, batch, piv, rp, st);
+  trsm<R, OP_N, true, true, false>(n2, nrhs, batch, cst(W), cst(CD), XY, rp, st);
+  trsm<R, OP_N, false, false, false>(n2, nrhs, batch, cst(W), cst(XY), XY, nullptr, st);
+  FROB_LAUNCH("aug_out", st, aug_out_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, cst(XY), X));
+}
+
 // ------------------------------------------------------------------ adjoint
 // grad M = -X^H G X^H for X = M^{-1} (d(M^{-1}) = -M^{-1} dM M^{-1}), as two
 // complex products, each by Gauss's three real multiplications (Sec. 2,

@@ -109,7 +109,7 @@ def load() -> ctypes.CDLL:
         lib.frob_inv_batched.restype = i32
         lib.frob_solve_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
         lib.frob_solve_workspace_bytes.restype = sz
-        for name in ("frob_solve", "cplx_lu_solve"):
+        for name in ("frob_solve", "cplx_lu_solve", "aug_real_solve"):
             f = getattr(lib, name)
             f.argtypes = [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, i32, vp, sz, vp, vp]
             f.restype = i32
@@ -529,6 +529,12 @@ def sylvester(a: torch.Tensor, b: torch.Tensor | None, c: torch.Tensor, prec: st
     if check:
         check_info(res.info(), "sylvester")
     return res
+
+
+def aug_real_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bool = True) -> Result:
+    """Solve M X = RHS through the 2n real augmented system [[A, -B], [B, A]]
+    by real LU (the third method of Sec. 5.2, a comparator)."""
+    return _solve("aug_real_solve", 2, m, rhs, prec, check)
 
 
 def inv_adjoint(x: torch.Tensor, g: torch.Tensor, prec: str | None = None) -> torch.Tensor:

@@ -21,6 +21,10 @@ Workloads (sizes follow the paper's experiments and the accuracy targets):
 * :func:`kappa_controlled` -- the accuracy generator of Sec. 5.1:
   A = Q Lam Q^T / ||Lam||_F with kappa(A) = kappa, and B likewise.
 * :func:`uniform01` -- A, B uniform on [0, 1] (the speed generator of Sec. 5.1).
+* :func:`hpd_kappa` -- the HPD accuracy generator of Sec. 5.6:
+  X = Q Lam Q^H / ||Lam||_F, Q from the QR factorization of a complex matrix
+  uniform on [-1, 1] (real and imaginary parts), lam_1 = kappa, lam_n = 1,
+  the rest uniform on [1, kappa].
 * :func:`sign_case`, :func:`polar_case`, :func:`sylvester_case` -- the
   "work backwards" generators of Sec. 5.3-5.5, whose answers are known by
   construction: X = Z J Z^{-1} with sign(X) = Z sign(Re J) Z^{-1}; X = U P
@@ -222,3 +226,20 @@ def sylvester_case(p: int, q: int, seed: int = 23, lyapunov: bool = False, re_lo
     y = _unif_c(g, (p, q))
     c = a @ y + y @ b
     return a, b, c, y
+
+
+def hpd_kappa(n: int, kappa: float = 10.0, seed: int = 24) -> np.ndarray:
+    """Hermitian positive definite X with kappa(X) = kappa (Sec. 5.6):
+    Q from QR of a matrix with real and imaginary parts uniform on [-1, 1],
+    Lam = diag(kappa, lam_2, ..., lam_{n-1}, 1) with the middle entries
+    uniform on [1, kappa]; X = Q Lam Q^H / ||Lam||_F, symmetrised."""
+    g = _rng(seed)
+    q, _ = np.linalg.qr(_unif_c(g, (n, n)))
+    lam = np.empty(n)
+    lam[0] = kappa
+    if n > 1:
+        lam[-1] = 1.0
+    if n > 2:
+        lam[1:-1] = g.uniform(1.0, kappa, n - 2)
+    x = (q * lam) @ q.conj().T / np.linalg.norm(lam)
+    return 0.5 * (x + x.conj().T)
