@@ -19,6 +19,8 @@ of Dai, Lim and Ye, "Complex matrix inversion via real matrix inversions":
                            three products, one addition.
 * :func:`frob_inv_b`    -- the formula for invertible B (Sec. 4.2, before
                            Lemma "rand Frob"), explicit real inversions.
+* :func:`bicomplex_inv` -- inverse of a bicomplex matrix A + jB (Sec. 2.4,
+                           m = 2) through its 2n complex embedding.
 * :func:`frob_inv_lu`   -- Algorithm "Frobenius inversion with LU
                            decomposition" (Sec. 4.1).
 * :func:`frob_inv_rand` -- Algorithm "Almost sure Frobenius inversion"
@@ -123,6 +125,7 @@ class Oracle:
             "orc_frob_inv_basic": [i, zp, zp, zp, zp, zp],
             "orc_frob_inv_lu": [i, zp, zp],
             "orc_frob_inv_b": [i, zp, zp],
+            "orc_bicomplex_inv": [i, zp, zp, zp, zp],
             "orc_frob_inv_rand": [i, zp, ctypes.c_double, zp],
             "orc_frob_inv_chol": [i, zp, zp],
             "orc_inv2x2": [zp, zp],
@@ -176,6 +179,19 @@ class Oracle:
         x = np.empty_like(m)
         _check("frob_inv_b", self.lib.orc_frob_inv_b(n, _ptr(m), _ptr(x)))
         return x
+
+    def bicomplex_inv(self, a, b):
+        """(A + jB)^{-1} = Y0 + jY1 for bicomplex matrices (j^2 = -1, j
+        commuting with i; the m = 2 iterated quadratic extension of Sec. 2.4),
+        from the inverse of the embedding [[A, -B], [B, A]].  Returns (Y0, Y1)."""
+        a, n = _prep(a)
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.complex128))
+        if b.shape != (n, n):
+            raise ValueError("A and B must both be n x n")
+        y0 = np.empty_like(a)
+        y1 = np.empty_like(a)
+        _check("bicomplex_inv", self.lib.orc_bicomplex_inv(n, _ptr(a), _ptr(b), _ptr(y0), _ptr(y1)))
+        return y0, y1
 
     def frob_inv_lu(self, m) -> np.ndarray:
         m, n = _prep(m)
@@ -305,6 +321,10 @@ def frob_inv_basic(m, stages: bool = False):
 
 def frob_inv_b(m):
     return load().frob_inv_b(m)
+
+
+def bicomplex_inv(a, b):
+    return load().bicomplex_inv(a, b)
 
 
 def frob_inv_lu(m):

@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORC_MUTANT plants one deliberate mistake (k = 1..14) so that a test can check
+/* ORC_MUTANT plants one deliberate mistake (k = 1..15) so that a test can check
  * that the pins catch it.  Product builds of the oracle use ORC_MUTANT = 0. */
 #ifndef ORC_MUTANT
 #define ORC_MUTANT 0
@@ -370,6 +370,40 @@ int orc_frob_inv_b(int n, const zc *m, zc *x)
     for (size_t t = 0; t < nn; ++t) x[t] = Y6[t] - (ORC_MUTANT == 14 ? -1.0 : 1.0) * I * Y5[t];
     free(w);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bicomplex matrices (the iterated quadratic extension of Sec. 2.4 with     */
+/* m = 2, xi_1^2 = xi_2^2 = -1; written X = A + jB with A, B complex and j   */
+/* commuting with i).  The map A + jB -> [[A, -B], [B, A]] is an injective   */
+/* algebra homomorphism into 2n x 2n complex matrices (j^2 = -1 matches the  */
+/* block structure), so X^{-1} = Y0 + jY1 is read off the inverse of the     */
+/* embedding, [[Y0, -Y1], [Y1, Y0]].  The inverse by complex LU.              */
+/* ------------------------------------------------------------------------- */
+int orc_bicomplex_inv(int n, const zc *a, const zc *b, zc *y0, zc *y1)
+{
+    if (n < 1) return -2;
+    const int n2 = 2 * n;
+    zc *e = malloc(sizeof(zc) * (size_t)n2 * n2), *ei = malloc(sizeof(zc) * (size_t)n2 * n2);
+    if (!e || !ei) { free(e); free(ei); return -1; }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const zc av = a[(size_t)i * n + k], bv = b[(size_t)i * n + k];
+            e[(size_t)i * n2 + k] = av;
+            e[(size_t)i * n2 + n + k] = -bv;
+            e[(size_t)(n + i) * n2 + k] = bv;
+            e[(size_t)(n + i) * n2 + n + k] = av;
+        }
+    int info = orc_cplx_lu_inv(n2, e, ei, 0);
+    if (info == 0)
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) {
+                y0[(size_t)i * n + k] = ei[(size_t)i * n2 + k];
+                y1[(size_t)i * n + k] = (ORC_MUTANT == 15 ? -1.0 : 1.0) * ei[(size_t)(n + i) * n2 + k];
+            }
+    free(e);
+    free(ei);
+    return info;
 }
 
 /* ------------------------------------------------------------------------- */

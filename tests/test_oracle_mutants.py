@@ -29,6 +29,7 @@ MUTANTS = {
     12: "Y = +1/2 of the top-right block instead of -1/2 (Sylvester)",
     13: "P = Q X instead of Q^H X (polar decomposition)",
     14: "Y6 + i Y5 instead of Y6 - i Y5 (formula for invertible B)",
+    15: "-Y1 read from the lower-left block (bicomplex inverse)",
 }
 
 
@@ -96,6 +97,12 @@ def _pin_failures(o) -> list:
     yf, _ = o.sylvester(a, b, c, 1e-13, 100)
     if np.abs(yf - y).max() > 1e-9 * np.abs(y).max():
         fails.append("sylvester closed form")
+    # bicomplex inverse: scalar closed form (a - jb) / (a^2 + b^2)
+    a1, b1 = 1.3 - 0.4j, 0.7 + 0.9j
+    y0, y1 = o.bicomplex_inv(np.array([[a1]]), np.array([[b1]]))
+    d = a1 * a1 + b1 * b1
+    if abs(y0[0, 0] - a1 / d) > 1e-14 or abs(y1[0, 0] + b1 / d) > 1e-14:
+        fails.append("bicomplex scalar")
     # Frobenius linear solve against LAPACK
     m = g.standard_normal((9, 9)) + 1j * g.standard_normal((9, 9))
     rhs = g.standard_normal((9, 2)) + 1j * g.standard_normal((9, 2))

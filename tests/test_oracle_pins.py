@@ -338,3 +338,41 @@ def test_frob_inv_b_is_frobenius_of_minus_i_m(oracle_lib):
     mp = m.imag - 1j * m.real
     assert np.abs(oracle.frob_inv_b(m) - (-1j) * oracle.frob_inv_basic(mp)).max() <= 1e-12 * np.abs(
         np.linalg.inv(m)).max()
+
+
+# ------------------------------------------------------------------ bicomplex matrices (Sec. 2.4, m = 2)
+
+
+def _bimul(a, b, c, d):
+    """(A + jB)(C + jD) = (AC - BD) + j(AD + BC), j^2 = -1, j commuting with i."""
+    return a @ c - b @ d, a @ d + b @ c
+
+
+def test_bicomplex_scalar_closed_form(oracle_lib):
+    """For commuting entries (a + jb)^{-1} = (a - jb) / (a^2 + b^2)."""
+    for a, b in ((2.0 + 1j, -0.5 + 0.25j), (0.3 - 2j, 1.1 + 0j), (1j, 0.0)):
+        y0, y1 = oracle.bicomplex_inv(np.array([[a]]), np.array([[b]]))
+        d = a * a + b * b
+        assert abs(y0[0, 0] - a / d) <= 1e-15 * abs(a / d) + 1e-300
+        assert abs(y1[0, 0] + b / d) <= 1e-15 * max(abs(b / d), 1e-300)
+
+
+@pytest.mark.parametrize("n", [2, 5, 17])
+def test_bicomplex_product_is_identity(oracle_lib, n):
+    g = np.random.default_rng(800 + n)
+    a = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    b = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    y0, y1 = oracle.bicomplex_inv(a, b)
+    for p0, p1 in (_bimul(a, b, y0, y1), _bimul(y0, y1, a, b)):
+        assert np.abs(p0 - np.eye(n)).max() <= 1e-12 and np.abs(p1).max() <= 1e-12
+
+
+def test_bicomplex_special_cases(oracle_lib):
+    """B = 0: Y0 = A^{-1}, Y1 = 0; A = 0: (jB)^{-1} = -j B^{-1}."""
+    g = np.random.default_rng(81)
+    a = g.standard_normal((6, 6)) + 1j * g.standard_normal((6, 6))
+    z = np.zeros_like(a)
+    y0, y1 = oracle.bicomplex_inv(a, z)
+    assert np.abs(y0 - np.linalg.inv(a)).max() <= 1e-12 * np.abs(np.linalg.inv(a)).max() and np.abs(y1).max() == 0.0
+    y0, y1 = oracle.bicomplex_inv(z, a)
+    assert np.abs(y0).max() <= 1e-13 and np.abs(y1 + np.linalg.inv(a)).max() <= 1e-12 * np.abs(np.linalg.inv(a)).max()
