@@ -338,6 +338,24 @@ frob_status frob_polar(int route, int n, int batch, const void* X, int64_t ldx, 
                        int64_t sq, void* P, int64_t ldp, int64_t sp, const frob_opts* opts, double eps, int kmax,
                        void* ws, size_t wsb, frob_info* info, int32_t* steps, void* stream);
 
+/*
+ * frob_inv_bicomplex -- inversion over the iterated quadratic extension of
+ * Sec. 2.4 with m = 2 (Theorem "GFiter"): X = A + jB with A, B complex n x n
+ * (complex128, or complex64 for FROB_FP32), j^2 = -1 and j commuting with i.
+ * Frobenius inversion over C: X1 = A^{-1}, X2 = X1 B, X4 = A + B X2,
+ * X5 = X4^{-1}, X6 = X2 X5, X^{-1} = Y0 + jY1 with Y0 = X5, Y1 = -X6; each
+ * complex inversion a frob_inv call (any precision it accepts), each complex
+ * product by Gauss's three real multiplications: 15 real products and 4 real
+ * inversions.  info[b]: the first failing inversion's record (bad_index as
+ * frob_inv reports it for A, plus 2n for A + B X2).  Y0 and Y1 must not
+ * overlap A, B or each other.  opts as for frob_inv (part FROB_PART_A, no
+ * almost sure option).  Workspace: frob_inv_bicomplex_workspace_bytes.
+ */
+size_t frob_inv_bicomplex_workspace_bytes(int n, int batch, int prec);
+frob_status frob_inv_bicomplex(int n, int batch, const void* A, int64_t lda, int64_t sa, const void* B, int64_t ldb,
+                               int64_t sb, void* Y0, int64_t ldy0, int64_t sy0, void* Y1, int64_t ldy1, int64_t sy1,
+                               const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* frob_status_str(int status);
 

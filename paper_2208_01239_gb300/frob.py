@@ -134,6 +134,11 @@ def load() -> ctypes.CDLL:
         lib.frob_sylvester.argtypes = [i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, i32, vp, i64, i64, vp, i64, i64,
                                        ctypes.POINTER(FrobOpts), dbl, i32, vp, sz, vp, vp, vp]
         lib.frob_sylvester.restype = i32
+        lib.frob_inv_bicomplex_workspace_bytes.argtypes = [i32, i32, i32]
+        lib.frob_inv_bicomplex_workspace_bytes.restype = sz
+        lib.frob_inv_bicomplex.argtypes = [i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
+                                           ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
+        lib.frob_inv_bicomplex.restype = i32
         lib.frob_profile_enable.argtypes = [i32]
         lib.frob_profile_enable.restype = None
         lib.frob_profile_report.argtypes = [ctypes.c_char_p, sz]
@@ -529,6 +534,40 @@ def sylvester(a: torch.Tensor, b: torch.Tensor | None, c: torch.Tensor, prec: st
     if check:
         check_info(res.info(), "sylvester")
     return res
+
+
+def frob_inv_bicomplex(a: torch.Tensor, b: torch.Tensor, prec: str = "fp64", check: bool = True,
+                       ns_tol: float = 1e-14):
+    """(A + jB)^{-1} = Y0 + jY1 for bicomplex matrices (j^2 = -1, j commuting
+    with i; the m = 2 iterated quadratic extension of Sec. 2.4): Frobenius
+    inversion over C with complex inversions by frob_inv and complex products
+    by Gauss multiplication.  Returns (Y0, Y1, info)."""
+    lib = load()
+    a3 = _batch3(a, "frob_inv_bicomplex", prec if prec in ("fp32", "fp64") else "fp64")
+    b3 = _batch3(b, "frob_inv_bicomplex", prec if prec in ("fp32", "fp64") else "fp64")
+    batch, n = a3.shape[0], a3.shape[-1]
+    if a3.shape != b3.shape or a3.shape[-2] != n:
+        raise ValueError("frob_inv_bicomplex: A and B must be (n, n) or (batch, n, n) of the same shape")
+    y0 = torch.empty((batch, n, n), dtype=a3.dtype, device=a3.device)
+    y1 = torch.empty_like(y0)
+    need = int(lib.frob_inv_bicomplex_workspace_bytes(n, batch, PREC[prec]))
+    if need == 0:
+        raise FrobError("frob_inv_bicomplex: unsupported precision", FROB_ERR_UNSUPPORTED)
+    ws, wp, wb = _ws(need, a3.device)
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=a3.device)
+    o = _opts(prec, ns_tol=ns_tol)
+    with torch.cuda.device(a3.device):
+        st = lib.frob_inv_bicomplex(n, batch, a3.data_ptr(), a3.stride(1), a3.stride(0), b3.data_ptr(), b3.stride(1),
+                                    b3.stride(0), y0.data_ptr(), y0.stride(1), y0.stride(0), y1.data_ptr(),
+                                    y1.stride(1), y1.stride(0), ctypes.byref(o), wp, wb, info.data_ptr(),
+                                    torch.cuda.current_stream(a3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"frob_inv_bicomplex: {status_str(st)}", st)
+    if check:
+        check_info(parse_info(info), "frob_inv_bicomplex")
+    if a.dim() == 2:
+        return y0[0], y1[0], info
+    return y0, y1, info
 
 
 def aug_real_solve(m: torch.Tensor, rhs: torch.Tensor, prec: str = "fp64", check: bool = True) -> Result:
