@@ -58,3 +58,76 @@ def test_host_only_calls(lib):
     assert lib.frob_inv(4, 1, 4096, 4, 16, 4096, 4, 16, None, 256, 1 << 20, 512, None) == 1   # in == out
     assert lib.frob_inv(4, 1, 16, 4, 16, 4096, 4, 16, None, 256, 8, 512, None) == 7          # ws too small
     assert lib.frob_inv(4, 1, 16, 4, 16, 4096, 4, 16, None, 257, 1 << 20, 512, None) == 7    # misaligned ws
+
+
+def test_opts_layout_matches_the_binding():
+    """frob_opts is 40 bytes (prec, almost_sure, seed, attempt, ns_max_iter,
+    ns_tol, part, reserved); the binding's ctypes mirror has the same size
+    and offsets."""
+    from paper_2208_01239_gb300 import frob
+    o = frob.FrobOpts
+    assert ctypes.sizeof(o) == 40
+    assert [o.seed.offset, o.ns_tol.offset, o.part.offset, o.reserved.offset] == [8, 24, 32, 36]
+
+
+def test_host_only_checks_of_the_newer_entry_points(lib):
+    """Argument and workspace errors of the part option, the Newton drivers,
+    the bicomplex inverse and the augmented solve return synchronously,
+    before any launch (no GPU is touched)."""
+    from paper_2208_01239_gb300 import frob
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    L = ctypes.CDLL(frob.library_path())
+    # frob_inv: part out of range, reserved set, part with the almost sure option
+    L.frob_inv.restype = i32
+    L.frob_inv.argtypes = [i32, i32, vp, i64, i64, vp, i64, i64, ctypes.POINTER(frob.FrobOpts), vp, sz, vp, vp]
+    for part, reserved, almost in ((3, 0, 0), (0, 1, 0), (1, 0, 1), (2, 0, 1)):
+        o = frob._opts("fp64", part="A")
+        o.part, o.reserved, o.almost_sure = part, reserved, almost
+        assert L.frob_inv(4, 1, 16, 4, 16, 4096, 4, 16, ctypes.byref(o), 256, 1 << 20, 512, None) == 1
+    # workspace sizes
+    L.frob_newton_workspace_bytes.restype = sz
+    L.frob_newton_workspace_bytes.argtypes = [i32, i32, i32, i32]
+    assert L.frob_newton_workspace_bytes(64, 2, 0, 0) > 2 * 64 * 64 * 16
+    assert L.frob_newton_workspace_bytes(64, 2, 0, 2) == 0          # no such route
+    assert L.frob_newton_workspace_bytes(64, 2, 3, 1) == 0          # mixed with the complex-LU route
+    assert L.frob_newton_workspace_bytes(600, 1, 3, 0) == 0         # mixed needs n <= 512
+    L.frob_solve_workspace_bytes.restype = sz
+    L.frob_solve_workspace_bytes.argtypes = [i32] * 5
+    assert L.frob_solve_workspace_bytes(2, 64, 1, 1, 0) >= 4 * 64 * 64 * 8  # the 2n x 2n real matrix
+    assert L.frob_solve_workspace_bytes(3, 64, 1, 1, 0) == 0
+    L.frob_inv_bicomplex_workspace_bytes.restype = sz
+    L.frob_inv_bicomplex_workspace_bytes.argtypes = [i32, i32, i32]
+    assert L.frob_inv_bicomplex_workspace_bytes(32, 1, 0) > L.frob_inv_bicomplex_workspace_bytes(32, 1, 1)
+    # frob_newton: bad kind, bad route, negative kmax, NaN eps, overlapping M / X, small workspace
+    L.frob_newton.restype = i32
+    L.frob_newton.argtypes = [i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, ctypes.c_double, i32, vp, sz, vp,
+                              vp, vp]
+    args = lambda kind=0, route=0, kmax=10, eps=1e-3, m=4096, x=1 << 20, ws=1 << 24, wsb=1 << 30: (
+        kind, route, 8, 1, m, 8, 64, x, 8, 64, None, eps, kmax, ws, wsb, 256, 512, None)
+    assert L.frob_newton(*args(kind=2)) == 1
+    assert L.frob_newton(*args(route=5)) == 1
+    assert L.frob_newton(*args(kmax=-1)) == 1
+    assert L.frob_newton(*args(eps=float("nan"))) == 1
+    assert L.frob_newton(*args(x=4096 + 16)) == 1                  # X overlaps M (and is not M itself)
+    assert L.frob_newton(*args(wsb=64)) == 7
+    # frob_sylvester: Lyapunov with p != q
+    L.frob_sylvester.restype = i32
+    L.frob_sylvester.argtypes = [i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, i32, vp, i64, i64, vp, i64, i64,
+                                 vp, ctypes.c_double, i32, vp, sz, vp, vp, vp]
+    assert L.frob_sylvester(0, 4, 5, 1, 4096, 4, 16, None, 5, 25, 1, 1 << 16, 5, 20, 1 << 20, 5, 20, None, 0.1, 10,
+                            1 << 24, 1 << 30, 256, 512, None) == 1
+    # frob_polar: Q overlapping X
+    L.frob_polar.restype = i32
+    L.frob_polar.argtypes = [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, ctypes.c_double, i32, vp,
+                             sz, vp, vp, vp]
+    assert L.frob_polar(0, 8, 1, 4096, 8, 64, 4096 + 32, 8, 64, 1 << 20, 8, 64, None, 1e-3, 10, 1 << 24, 1 << 30,
+                        256, 512, None) == 1
+    # frob_inv_bicomplex: Y0 overlapping Y1, and the part option
+    L.frob_inv_bicomplex.restype = i32
+    L.frob_inv_bicomplex.argtypes = [i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
+                                     ctypes.POINTER(frob.FrobOpts), vp, sz, vp, vp]
+    assert L.frob_inv_bicomplex(8, 1, 4096, 8, 64, 1 << 16, 8, 64, 1 << 20, 8, 64, (1 << 20) + 64, 8, 64, None,
+                                1 << 24, 1 << 30, 512, None) == 1
+    o = frob._opts("fp64", part="B")
+    assert L.frob_inv_bicomplex(8, 1, 4096, 8, 64, 1 << 16, 8, 64, 1 << 20, 8, 64, 1 << 21, 8, 64, ctypes.byref(o),
+                                1 << 24, 1 << 30, 512, None) == 1
