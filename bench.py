@@ -328,6 +328,30 @@ def measure_accuracy(frob, dev):
     return out
 
 
+def measure_config3_fp32(frob, dev):
+    """The ill-conditioned construction (A = I, B = Q N Q^T, s = 1 - 1e-6,
+    kappa(M) ~ 2e6) in FP32 at n = 512: relative forward error (max norm)
+    of Frobenius inversion and of complex LU against the FP64 inverse of the
+    FP32-rounded input (LAPACK through numpy on the host), and the residual
+    ||M X - I||_F / (||M||_F ||X||_F).  S = (1 - s^2) I ~ 2e-6 I is formed
+    by cancellation, which FP32 cannot resolve."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+    n = 512
+    m, _ = W.ill_conditioned(n, seed=5)
+    m32 = m.astype(np.complex64)
+    m64 = m32.astype(np.complex128)
+    ref = np.linalg.inv(m64)
+    out = {"n": n, "kappa": float(np.linalg.cond(m64))}
+    for name, f in (("frob_inv", frob.frob_inv), ("cplx_lu_inv", frob.cplx_lu_inv)):
+        x = f(torch.from_numpy(m32).to(dev), prec="fp32", check=False).x.cpu().numpy().astype(np.complex128)
+        r = m64 @ x - np.eye(n)
+        out[name] = {"forward_error": float(np.abs(x - ref).max() / np.abs(ref).max()),
+                     "residual_fro": float(np.linalg.norm(r) / (np.linalg.norm(m64) * np.linalg.norm(x)))}
+    return out
+
+
 def measure_solve(frob, dev, steps):
     """Linear systems (Sec. 5.2): 16 systems of order 512, one right-hand
     side, A and B from the kappa = 10 generator of Sec. 5.1 and x, y uniform
@@ -548,6 +572,7 @@ def main():
     solve = None if args.no_batched else measure_solve(frob, dev, 3)
     newton = None if (args.no_newton or args.no_batched) else measure_newton(frob, dev)
     accuracy = None if (args.no_accuracy or args.no_batched) else measure_accuracy(frob, dev)
+    config3_fp32 = None if (args.no_accuracy or args.no_batched) else measure_config3_fp32(frob, dev)
 
     # end to end through the public API with host buffers
     def e2e_step():
@@ -601,6 +626,7 @@ def main():
         "linear_solve": solve,
         "newton_drivers": newton,
         "accuracy_kappa10": accuracy,
+        "ill_conditioned_fp32": config3_fp32,
         "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),
