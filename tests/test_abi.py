@@ -131,3 +131,24 @@ def test_host_only_checks_of_the_newer_entry_points(lib):
     o = frob._opts("fp64", part="B")
     assert L.frob_inv_bicomplex(8, 1, 4096, 8, 64, 1 << 16, 8, 64, 1 << 20, 8, 64, 1 << 21, 8, 64, ctypes.byref(o),
                                 1 << 24, 1 << 30, 512, None) == 1
+
+
+def test_bindings_reject_bad_inputs_before_calling_the_library():
+    """The Python binding's own checks (host tensors, dtypes, shapes, option
+    names) raise before anything reaches the library; no GPU needed."""
+    import torch
+    from paper_2208_01239_gb300 import frob
+    cpu = torch.zeros((4, 4), dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        frob.sign(cpu)
+    with pytest.raises(TypeError):
+        frob.polar(cpu)
+    with pytest.raises(TypeError):
+        frob.sylvester(cpu, cpu, cpu)
+    with pytest.raises(TypeError):
+        frob.frob_inv_bicomplex(cpu, cpu)
+    with pytest.raises(KeyError):
+        frob._opts("fp64", part="C")
+    assert frob.ROUTE == {"frob": 0, "cplx_lu": 1} and frob.PART == {"A": 0, "B": 1, "auto": 2}
+    o = frob._opts("fp32", part="auto")
+    assert (o.prec, o.part, o.reserved, o.almost_sure) == (frob.PREC["fp32"], 2, 0, 0)
