@@ -1,9 +1,12 @@
 // Batched inversion of matrices of different orders in one call.
 //
-// Every matrix M_i (order n_i) is embedded as M_i (+) I in a bucket of order
-// N = 32 ceil(n_i / 32): (M (+) I)^{-1} = M^{-1} (+) I, the identity block
-// never takes part in pivoting (its columns hold a single 1 on the diagonal)
-// and keeps Hermitian positive definite input Hermitian positive definite.
+// Every matrix M_i (order n_i) is embedded as M_i (+) cI in a bucket of order
+// N = 32 ceil(n_i / 32): (M (+) cI)^{-1} = M^{-1} (+) c^{-1} I, the padding
+// block never takes part in pivoting (its columns hold a single nonzero on
+// the diagonal).  c = 1 keeps Hermitian positive definite input Hermitian
+// positive definite; with the part options of frob_inv c = i (B factored) or
+// 1 + i (either part), so that the factored real part of the padding is
+// invertible.
 // Each bucket then runs the uniform strided-batch path (frob_inv,
 // frob_inv_hpd or a baseline), and the results and info records are
 // scattered back.  The slot of each matrix in its bucket is computed on the
@@ -110,7 +113,7 @@ __global__ void map_kernel(int batch, const int32_t* n_dev, BucketTable t, int* 
 
 template <typename C>
 __global__ void gather_kernel(int N, int offset, const int* map, const int32_t* n_dev, const void* const* M,
-                              const int64_t* ldm, C* pin) {
+                              const int64_t* ldm, C* pin, C pad) {
   const int s = blockIdx.z;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)N * N) return;
@@ -121,7 +124,7 @@ __global__ void gather_kernel(int N, int offset, const int* map, const int32_t* 
   if (r < n && c < n)
     v = static_cast<const C*>(M[i])[(int64_t)r * ldm[i] + c];
   else if (r == c)
-    v = one_v<C>();
+    v = pad;
   pin[(int64_t)s * N * N + e] = v;
 }
 
@@ -184,6 +187,11 @@ extern "C" frob_status frob_inv_batched(int op, int batch, const int32_t* n_host
   }
   FROB_LAUNCH("batched_map", st, map_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, n_dev, t, L.map));
   const bool f32 = o.prec == FROB_FP32;
+  // the padding block's diagonal: its factored real part must be invertible
+  // (i for FROB_PART_B, 1 + i for FROB_PART_AUTO so that either part is;
+  // 1 otherwise); its inverse is discarded
+  const double pr = (op == FROB_OP_INV && o.part == FROB_PART_B) ? 0.0 : 1.0;
+  const double pi = (op == FROB_OP_INV && o.part != FROB_PART_A) ? 1.0 : 0.0;
   for (int b = 0; b < p.nb; ++b) {
     const int N = p.N[b], cnt = p.count[b];
     const int64_t NN = (int64_t)N * N;
@@ -191,11 +199,11 @@ extern "C" frob_status frob_inv_batched(int op, int batch, const int32_t* n_host
     if (f32)
       FROB_LAUNCH("batched_gather", st,
                   gather_kernel<zf><<<g, 256, 0, st>>>(N, p.offset[b], L.map, n_dev, M_dev, ldm_dev,
-                                                       reinterpret_cast<zf*>(L.pin)));
+                                                       reinterpret_cast<zf*>(L.pin), zf{(float)pr, (float)pi}));
     else
       FROB_LAUNCH("batched_gather", st,
                   gather_kernel<zd><<<g, 256, 0, st>>>(N, p.offset[b], L.map, n_dev, M_dev, ldm_dev,
-                                                       reinterpret_cast<zd*>(L.pin)));
+                                                       reinterpret_cast<zd*>(L.pin), zd{pr, pi}));
     frob_status s;
     switch (op) {
       case FROB_OP_INV:

@@ -299,7 +299,7 @@ class Batched:
     captured with ``torch.cuda.graph`` after one eager call."""
 
     def __init__(self, ns, op: str = "frob_inv", prec: str = "fp64", device="cuda", ns_tol: float = 1e-14,
-                 ns_max_iter: int = 8):
+                 ns_max_iter: int = 8, part: str = "A"):
         lib = load()
         self.lib = lib
         self.ns = [int(n) for n in ns]
@@ -321,7 +321,7 @@ class Batched:
         self.ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
         self.pad = (-self.ws.data_ptr()) % 256
         self.info_dev = torch.zeros((self.batch, 32), dtype=torch.uint8, device=dev)
-        self.opts = _opts(prec)
+        self.opts = _opts(prec, part=part)
         self.opts.ns_tol = ns_tol
         self.opts.ns_max_iter = ns_max_iter
 
@@ -338,11 +338,12 @@ class Batched:
         return parse_info(self.info_dev)
 
 
-def frob_inv_batched(mats, op: str = "frob_inv", prec: str = "fp64", check: bool = True):
+def frob_inv_batched(mats, op: str = "frob_inv", prec: str = "fp64", check: bool = True, part: str = "A"):
     """Invert a list of square complex matrices of different orders in one
-    call; returns (list of inverses, info records)."""
+    call; returns (list of inverses, info records).  ``part`` as for
+    :func:`frob_inv` (op "frob_inv" only)."""
     plan = Batched([m.shape[-1] for m in mats], op=op, prec=prec,
-                   device=mats[0].device if mats[0].is_cuda else "cuda")
+                   device=mats[0].device if mats[0].is_cuda else "cuda", part=part)
     for dst, src in zip(plan.inputs, mats):
         dst.copy_(src)
     plan.run()

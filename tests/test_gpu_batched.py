@@ -113,3 +113,24 @@ def test_config4_uneven_1024_mixed(F):
         res = metrics.residual_fro(m, x)
         assert metrics.forward_error(x, oracle.cplx_lu_inv(m)) <= 32 * m.shape[0] * kappa * U["fp64"] + \
             4 * np.sqrt(m.shape[0]) * kappa * res
+
+
+@pytest.mark.parametrize("part", ["B", "auto"])
+def test_batched_part_options(F, part):
+    """The part options through the uneven-order driver: the padding block
+    is i I (B factored) or (1 + i) I (either part), so padded buckets stay
+    invertible in the factored part; a matrix with a singular real part is
+    inverted, every result against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle import metrics
+    g = np.random.default_rng(55)
+    sizes = [37, 64, 5, 100]
+    mats = [g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)) for n in sizes]
+    mats[0][:, 4] = mats[0][:, 4].imag * 1j  # real part of column 4 is zero: A singular
+    outs, info = F.frob_inv_batched([torch.from_numpy(m).cuda() for m in mats], part=part)
+    assert list(info["status"]) == [F.FROB_OK] * len(sizes)
+    for m, x in zip(mats, outs):
+        n = m.shape[0]
+        assert metrics.forward_error(x.cpu().numpy(), oracle.cplx_lu_inv(m)) <= 32 * n * np.linalg.cond(m) * 2.0 ** -53

@@ -126,3 +126,13 @@ def test_zero_steps_and_singular(F):
     assert np.array_equal(r.out.cpu().numpy()[1], xs[1])
     good = F.sign(torch.from_numpy(x).cuda(), eps=1e-10).out.cpu().numpy()
     assert np.array_equal(r.out.cpu().numpy()[0], good)
+
+
+def test_polar_and_sylvester_fp32(F):
+    x, u, p = W.polar_case(40, seed=390)
+    r = F.polar(torch.from_numpy(x.astype(np.complex64)).cuda(), prec="fp32", eps=1e-4)
+    q, pm = (t.cpu().numpy().astype(np.complex128) for t in r.out)
+    assert np.abs(q - u).max() <= 1e-3 and _rel(pm, p) <= 1e-3
+    a, b, c, y = W.sylvester_case(20, 12, seed=391)
+    ry = F.sylvester(*(torch.from_numpy(t.astype(np.complex64)).cuda() for t in (a, b, c)), prec="fp32", eps=1e-4)
+    assert _rel(ry.out.cpu().numpy().astype(np.complex128), y) <= 1e-3
