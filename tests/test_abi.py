@@ -152,3 +152,29 @@ def test_bindings_reject_bad_inputs_before_calling_the_library():
     assert frob.ROUTE == {"frob": 0, "cplx_lu": 1} and frob.PART == {"A": 0, "B": 1, "auto": 2}
     o = frob._opts("fp32", part="auto")
     assert (o.prec, o.part, o.reserved, o.almost_sure) == (frob.PREC["fp32"], 2, 0, 0)
+
+
+def test_batched_plan_sizes(lib):
+    """The uneven-batch planner (host only): buckets of order 32 ceil(n/32);
+    a list whose orders share a bucket needs less workspace than the same
+    count spread over more buckets' worth of padding; an order < 1 or more
+    than 64 distinct buckets is refused (0); the mixed precisions need
+    n <= 512."""
+    import numpy as np
+    i32, sz, vp = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+    f = lib.frob_inv_batched_workspace_bytes
+    f.restype = sz
+    f.argtypes = [i32, i32, vp, i32]
+
+    def ws(ns, op=0, prec=0):
+        a = np.ascontiguousarray(np.array(ns, dtype=np.int32))
+        return f(op, len(ns), a.ctypes.data, prec)
+
+    assert ws([33, 40, 64]) > 0
+    assert ws([33, 40, 64]) == ws([64, 64, 64])                           # one bucket of order 64 either way
+    assert ws([31, 33]) < ws([31, 65])                                    # buckets 32 + 64 vs 32 + 96
+    assert ws([0, 5]) == 0
+    assert ws([32 * k for k in range(1, 66)]) == 0                        # 65 distinct buckets
+    assert ws([32 * k for k in range(1, 65)]) > 0                         # 64 are allowed
+    assert ws([600], prec=3) == 0 and ws([500], prec=3) > 0               # mixed: n <= 512
+    assert ws([10], op=7) == 0
