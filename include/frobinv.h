@@ -380,6 +380,24 @@ uint64_t frob_kernel_launches(void);
 void frob_profile_enable(int on);
 size_t frob_profile_report(char* buf, size_t len);
 
+/* Autotuning of the stream split (off by default).  A batch of two or more
+ * matrices normally runs as two slices on two internal streams; with
+ * frob_autotune_enable(1), the first call of frob_inv, frob_inv_hpd,
+ * cplx_lu_inv or cplx_chol_inv for a given (operation, precision, n, batch)
+ * runs three times (an untimed two-slice warm-up, then one slice and two
+ * slices timed with CUDA events, with a host synchronisation) and caches the
+ * faster split, which later calls use.  The FP64 / FP32 results do not
+ * depend on the split (every matrix runs the same kernels); the mixed
+ * precisions' only through the order of atomic residual sums.  No tuning
+ * happens during a CUDA-graph capture or while the per-kernel profiler is
+ * on, and not when the workspace is too small for the one-slice layout.
+ * frob_autotune_report writes {"op,prec,n,batch": [slices, ms_one_slice,
+ * ms_two_slices], ...} like frob_profile_report; frob_autotune_clear empties
+ * the cache. */
+void frob_autotune_enable(int on);
+void frob_autotune_clear(void);
+size_t frob_autotune_report(char* buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

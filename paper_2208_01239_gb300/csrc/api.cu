@@ -158,11 +158,83 @@ template <class WsOf> size_t split_ws(int batch, WsOf ws_of) {
   for (int k = 0; k < NSPLIT; ++k) total += round256(ws_of(slice_count(batch, k)));
   return total;
 }
+// Autotuning of the split (opt-in, frob_autotune_enable): per (operation,
+// precision, n, batch) the call is timed once as one slice and once as two
+// (after an untimed two-slice run), and the faster is cached for later calls.
+// Every matrix goes through the same kernels whatever the split, so the
+// FP64 / FP32 results do not depend on the choice (the mixed precisions'
+// residual sums only through the order of their atomic additions).  No
+// tuning while a graph capture or the per-kernel profiler is active.
+struct TuneKey {
+  int op, prec, n, batch;
+  bool operator<(const TuneKey& o) const {
+    if (op != o.op) return op < o.op;
+    if (prec != o.prec) return prec < o.prec;
+    if (n != o.n) return n < o.n;
+    return batch < o.batch;
+  }
+};
+struct TuneRec {
+  int slices;
+  float ms_one, ms_two;
+};
+std::atomic<int> g_tune_on{0};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneRec> g_tune;
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
 // run(first, count, workspace, stream) per slice.  While per-kernel profiling
 // is on, the slices run one after the other on the caller's stream, so that
 // the events around a launch time that kernel alone.
-template <class WsOf, class Run> void split_run(int batch, void* ws, cudaStream_t st, WsOf ws_of, Run run) {
+template <class WsOf, class Run> void split_slices(int slices, int batch, void* ws, cudaStream_t st, WsOf ws_of, Run run);
+
+template <class WsOf, class Run>
+void split_run(int batch, void* ws, cudaStream_t st, WsOf ws_of, Run run, const TuneKey* key = nullptr,
+               size_t wsb = 0) {
   if (batch < NSPLIT) {
+    run(0, batch, ws, st);
+    return;
+  }
+  int slices = NSPLIT;
+  if (key && g_tune_on.load(std::memory_order_relaxed)) {
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(*key);
+      if (it != g_tune.end()) {
+        slices = it->second.slices;
+        found = true;
+      }
+    }
+    if (!found && !g_prof_on.load(std::memory_order_relaxed) && !capturing(st) && round256(ws_of(batch)) <= wsb) {
+      cudaEvent_t ev[3];
+      for (auto& e : ev) cudaEventCreate(&e);
+      split_slices(NSPLIT, batch, ws, st, ws_of, run);  // warm-up (first-use setup)
+      cudaEventRecord(ev[0], st);
+      split_slices(1, batch, ws, st, ws_of, run);
+      cudaEventRecord(ev[1], st);
+      split_slices(NSPLIT, batch, ws, st, ws_of, run);  // the output of this run stands
+      cudaEventRecord(ev[2], st);
+      float t1 = 0.f, t2 = 0.f;
+      if (cudaEventSynchronize(ev[2]) == cudaSuccess) {
+        cudaEventElapsedTime(&t1, ev[0], ev[1]);
+        cudaEventElapsedTime(&t2, ev[1], ev[2]);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[*key] = TuneRec{t1 <= t2 ? 1 : NSPLIT, t1, t2};
+      }
+      for (auto& e : ev) cudaEventDestroy(e);
+      return;
+    }
+  }
+  split_slices(slices, batch, ws, st, ws_of, run);
+}
+
+template <class WsOf, class Run> void split_slices(int slices, int batch, void* ws, cudaStream_t st, WsOf ws_of, Run run) {
+  if (slices < NSPLIT) {
     run(0, batch, ws, st);
     return;
   }
@@ -244,13 +316,14 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
     if (o.almost_sure) return FROB_ERR_UNSUPPORTED;
     if (n > 512) return FROB_ERR_UNSUPPORTED;
     frob_status ms = FROB_OK;
+    const TuneKey key{FROB_OP_INV, o.prec, n, batch};
     split_run(batch, ws, st, [&](int b) { return mixed::mixed_ws(n, b); },
               [&](int first, int count, void* w, cudaStream_t s2) {
                 frob_status r = mixed::mixed_run(n, count, in_view<zd>(M, ldm, sm).at_batch(first),
                                                  out_view<zd>(X, ldx, sx).at_batch(first), o, w, info + first, s2,
                                                  false);
                 if (r != FROB_OK) ms = r;
-              });
+              }, &key, wsb);
     return ms != FROB_OK ? ms : launched();
   }
   // (the almost-sure draw of mu depends on the matrix index: one slice)
@@ -263,12 +336,13 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
       frob_lu_run<double>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first),
                           o, w, info + first, s2);
   };
+  const TuneKey key{FROB_OP_INV, o.prec, n, batch};
   if (sb == 1)
     run(0, batch, ws, st);
   else
     split_run(batch, ws, st, [&](int b) {
       return o.prec == FROB_FP32 ? frob_lu_ws<float>(n, b, nullptr, nullptr) : frob_lu_ws<double>(n, b, nullptr, nullptr);
-    }, run);
+    }, run, &key, wsb);
   return launched();
 }
 
@@ -283,15 +357,17 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
   if (mixed_prec(o.prec)) {
     if (n > 512) return FROB_ERR_UNSUPPORTED;
     frob_status ms = FROB_OK;
+    const TuneKey key{FROB_OP_INV_HPD, o.prec, n, batch};
     split_run(batch, ws, st, [&](int b) { return mixed::mixed_ws(n, b); },
               [&](int first, int count, void* w, cudaStream_t s2) {
                 frob_status r = mixed::mixed_run(n, count, in_view<zd>(M, ldm, sm).at_batch(first),
                                                  out_view<zd>(X, ldx, sx).at_batch(first), o, w, info + first, s2,
                                                  true);
                 if (r != FROB_OK) ms = r;
-              });
+              }, &key, wsb);
     return ms != FROB_OK ? ms : launched();
   }
+  const TuneKey key{FROB_OP_INV_HPD, o.prec, n, batch};
   split_run(batch, ws, st, [&](int b) {
     return o.prec == FROB_FP32 ? frob_chol_ws<float>(n, b, nullptr, nullptr) : frob_chol_ws<double>(n, b, nullptr, nullptr);
   }, [&](int first, int count, void* w, cudaStream_t s2) {
@@ -301,7 +377,7 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
     else
       frob_chol_run<double>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first),
                             w, info + first, s2);
-  });
+  }, &key, wsb);
   return launched();
 }
 
@@ -312,6 +388,7 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
                                frob_workspace_bytes(FROB_OP_CPLX_LU, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TuneKey key{FROB_OP_CPLX_LU, prec, n, batch};
   split_run(batch, ws, st, [&](int b) {
     return prec == FROB_FP32 ? cplx_lu_ws<zf>(n, b, nullptr, nullptr) : cplx_lu_ws<zd>(n, b, nullptr, nullptr);
   }, [&](int first, int count, void* w, cudaStream_t s2) {
@@ -321,7 +398,7 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
     else
       cplx_lu_run<zd>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first), w,
                       info + first, s2);
-  });
+  }, &key, wsb);
   return launched();
 }
 
@@ -332,6 +409,7 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
                                frob_workspace_bytes(FROB_OP_CPLX_CHOL, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TuneKey key{FROB_OP_CPLX_CHOL, prec, n, batch};
   split_run(batch, ws, st, [&](int b) {
     return prec == FROB_FP32 ? cplx_chol_ws<zf>(n, b, nullptr, nullptr) : cplx_chol_ws<zd>(n, b, nullptr, nullptr);
   }, [&](int first, int count, void* w, cudaStream_t s2) {
@@ -341,7 +419,7 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
     else
       cplx_chol_run<zd>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first), w,
                         info + first, s2);
-  });
+  }, &key, wsb);
   return launched();
 }
 
@@ -453,6 +531,36 @@ const char* frob_status_str(int status) {
 const char* frob_version(void) { return "frobinv 0.1 sm_103a"; }
 
 uint64_t frob_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void frob_autotune_enable(int on) { g_tune_on.store(on ? 1 : 0); }
+
+void frob_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+size_t frob_autotune_report(char* buf, size_t len) {
+  std::string out = "{";
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool first = true;
+    for (const auto& kv : g_tune) {
+      char item[160];
+      std::snprintf(item, sizeof(item), "%s\"%d,%d,%d,%d\": [%d, %.6g, %.6g]", first ? "" : ", ", kv.first.op,
+                    kv.first.prec, kv.first.n, kv.first.batch, kv.second.slices, (double)kv.second.ms_one,
+                    (double)kv.second.ms_two);
+      out += item;
+      first = false;
+    }
+  }
+  out += "}";
+  if (buf && len > 0) {
+    const size_t k = out.size() < len - 1 ? out.size() : len - 1;
+    std::memcpy(buf, out.data(), k);
+    buf[k] = '\0';
+  }
+  return out.size() + 1;
+}
 
 void frob_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

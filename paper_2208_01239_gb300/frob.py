@@ -20,6 +20,7 @@ Each takes a complex tensor of shape (n, n) or (batch, n, n), complex128 for
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -139,12 +140,38 @@ def load() -> ctypes.CDLL:
         lib.frob_inv_bicomplex.argtypes = [i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                                            ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
         lib.frob_inv_bicomplex.restype = i32
+        lib.frob_autotune_enable.argtypes = [i32]
+        lib.frob_autotune_enable.restype = None
+        lib.frob_autotune_clear.argtypes = []
+        lib.frob_autotune_clear.restype = None
+        lib.frob_autotune_report.argtypes = [ctypes.c_char_p, sz]
+        lib.frob_autotune_report.restype = sz
         lib.frob_profile_enable.argtypes = [i32]
         lib.frob_profile_enable.restype = None
         lib.frob_profile_report.argtypes = [ctypes.c_char_p, sz]
         lib.frob_profile_report.restype = sz
         _lib = lib
         return lib
+
+
+def autotune(on: bool = True):
+    """Turn the autotuning of the stream split on or off (see
+    frob_autotune_enable in include/frobinv.h)."""
+    load().frob_autotune_enable(1 if on else 0)
+
+
+def autotune_clear():
+    load().frob_autotune_clear()
+
+
+def autotune_report() -> dict:
+    """{(op, prec, n, batch): (slices, ms_one_slice, ms_two_slices)}."""
+    lib = load()
+    need = int(lib.frob_autotune_report(None, 0))
+    buf = ctypes.create_string_buffer(need)
+    lib.frob_autotune_report(buf, need)
+    raw = json.loads(buf.value.decode())
+    return {tuple(int(v) for v in k.split(",")): (int(x[0]), float(x[1]), float(x[2])) for k, x in raw.items()}
 
 
 def profile_enable(on: bool = True):

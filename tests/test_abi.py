@@ -178,3 +178,14 @@ def test_batched_plan_sizes(lib):
     assert ws([32 * k for k in range(1, 65)]) > 0                         # 64 are allowed
     assert ws([600], prec=3) == 0 and ws([500], prec=3) > 0               # mixed: n <= 512
     assert ws([10], op=7) == 0
+
+
+def test_autotune_cache_host_side():
+    """The split autotuner's cache is empty until a tuned call runs, and
+    clearing it is a host operation."""
+    from paper_2208_01239_gb300 import frob
+    frob.autotune_clear()
+    assert frob.autotune_report() == {}
+    frob.autotune(True)
+    frob.autotune(False)
+    assert frob.autotune_report() == {}

@@ -53,3 +53,43 @@ def test_slice_info_offsets(F):
     info = r.info()
     assert list(info["status"][:3]) == [F.FROB_OK] * 3
     assert info["status"][3] == F.FROB_ERR_SINGULAR
+
+
+def test_autotuned_split_gives_the_same_results(F):
+    """With the split autotuner on, the first call of a new shape runs the
+    one- and two-slice forms and caches the faster; results are bit for bit
+    those of the default split, and a graph capture does not tune."""
+    ms = W.hpd(96, 6, seed=77)
+    m = torch.from_numpy(ms).cuda()
+    ref = F.frob_inv_hpd(m).x.cpu().numpy()
+    F.autotune_clear()
+    F.autotune(True)
+    try:
+        first = F.frob_inv_hpd(m).x.cpu().numpy()
+        second = F.frob_inv_hpd(m).x.cpu().numpy()
+        rep = F.autotune_report()
+        key = (F.OP["frob_inv_hpd"], F.PREC["fp64"], 96, 6)
+        assert key in rep and rep[key][0] in (1, 2) and rep[key][1] > 0 and rep[key][2] > 0
+        assert np.array_equal(first, ref) and np.array_equal(second, ref)
+        # a new shape under graph capture is not tuned
+        m5 = torch.from_numpy(W.hpd(96, 5, seed=78)).cuda()
+        out = torch.empty_like(m5)
+        ws = torch.empty(F.workspace_bytes("frob_inv_hpd", 96, 5) + 256, dtype=torch.uint8, device="cuda")
+        info = torch.zeros((5, 32), dtype=torch.uint8, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            F.frob_inv_hpd(m5, out=out, ws=ws, info=info, check=False)  # eager first call: tunes this shape
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        F.autotune_clear()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            F.frob_inv_hpd(m5, out=out, ws=ws, info=info, check=False)
+        assert F.autotune_report() == {}
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), F.frob_inv_hpd(m5).x.cpu().numpy())
+    finally:
+        F.autotune(False)
+        F.autotune_clear()
