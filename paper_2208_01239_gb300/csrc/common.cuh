@@ -11,6 +11,9 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <cuda_runtime.h>
 
 #include "../../include/frobinv.h"
@@ -161,6 +164,22 @@ enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
 // time can be read back with frob_profile_report.
 void launch_begin(const char* name, cudaStream_t st);
 void launch_end(const char* name, cudaStream_t st);
+// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) once per
+// (kernel, device, bytes): the attribute belongs to the function on the
+// current device, so a process that drives several GPUs sets it on each.
+inline bool smem_attr_needed(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> seen;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  return seen.insert(std::make_tuple(fn, dev, bytes)).second;
+}
+template <typename F> inline void set_smem_attr(F* kernel, int bytes) {
+  if (smem_attr_needed(reinterpret_cast<const void*>(kernel), bytes))
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 #define FROB_LAUNCH(NAME, ST, ...)    \
   do {                                \
     ::frob::launch_begin(NAME, ST);   \

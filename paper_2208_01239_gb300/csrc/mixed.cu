@@ -231,11 +231,7 @@ __global__ void check_kernel(int batch, int it, int last, double tol, const doub
 // no second), at most one per tile.
 template <int MODE>
 void launch_cgemm(const CUtensorMap& ma, const CUtensorMap& mb, const oz::OzArgs& a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(oz::oz_cgemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
-    attr = true;
-  }
+  set_smem_attr(oz::oz_cgemm_kernel<MODE>, oz::SMEM_BYTES);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

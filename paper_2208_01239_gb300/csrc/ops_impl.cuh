@@ -171,12 +171,7 @@ inline void mirror(int n, int batch, MatB<T> A, cudaStream_t st) {
 
 template <typename T, int OPT, bool LOWER, bool UNIT, bool RHS_I>
 inline void trsm_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SmemTrsm<T>));
-    done = true;
-  }
+  set_smem_attr(trsm_step_kernel<T, OPT, LOWER, UNIT, RHS_I>, (int)sizeof(SmemTrsm<T>));
 }
 
 // op(T) X = B over all block rows (in order of the substitution)
@@ -205,12 +200,7 @@ inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm,
 // the same layout (its lower blocks are overwritten).
 template <typename T, bool UNIT>
 inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(trtri_diag_kernel<T, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SmemTrsm<T>));
-    attr = true;
-  }
+  set_smem_attr(trtri_diag_kernel<T, UNIT>, (int)sizeof(SmemTrsm<T>));
   static const std::string name = std::string("trtri_diag<") + type_tag<T>() + ">";
   const int nblk = (n + TB - 1) / TB;
   FROB_LAUNCH(name.c_str(), st,
@@ -236,13 +226,8 @@ inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cu
 }
 
 template <typename T> inline void panel_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(getrf_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX);
-    cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)laswp_trsm_smem<T>());
-    done = true;
-  }
+  set_smem_attr(getrf_panel_kernel<T>, (int)PANEL_SMEM_MAX);
+  set_smem_attr(laswp_trsm_kernel<T>, (int)laswp_trsm_smem<T>());
 }
 
 template <typename T> inline const char* getrf_panel_name() {
@@ -259,11 +244,7 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
   if constexpr (std::is_same<T, float>::value) {
     if (n <= SLU_MAX) {
       // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(getrf_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLU_SMEM);
-        attr = true;
-      }
+      set_smem_attr(getrf_small_kernel<float>, SLU_SMEM);
       FROB_LAUNCH("getrf_small<f32>", st,
                   getrf_small_kernel<float><<<batch, SLU_THREADS, SLU_SMEM, st>>>(n, A, piv, info, info_off));
       return;
@@ -309,11 +290,7 @@ inline void potrf(int n, int batch, MatB<T> A, frob_info* info, int info_off, cu
   if constexpr (std::is_same<T, float>::value) {
     if (n <= SCHOL_MAX) {
       // one CTA per matrix (its panels, row solves and trailing updates between CTA barriers)
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(potrf_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCHOL_SMEM);
-        attr = true;
-      }
+      set_smem_attr(potrf_small_kernel<float>, SCHOL_SMEM);
       FROB_LAUNCH("potrf_small<f32>", st,
                   potrf_small_kernel<float><<<batch, SCHOL_THREADS, SCHOL_SMEM, st>>>(n, A, info, info_off));
       return;

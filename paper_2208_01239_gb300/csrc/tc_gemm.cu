@@ -72,12 +72,7 @@ template <int KIND, int BN, int STAGES, class Epi>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, int batch, Epi epi, int* err,
                    cudaStream_t st) {
   using S = TcSmem<BN, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         S::BYTES);
-    attr = true;
-  }
+  set_smem_attr(tc_gemm_kernel<KIND, BN, STAGES, Epi>, S::BYTES);
   // persistent: one CTA per SM (the shared memory admits no second), at most one per tile
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
