@@ -1,5 +1,10 @@
 // C-ABI entry points of libfrobinv (declared in include/frobinv.h): argument
-// checks, workspace sizing and dispatch to the per-precision drivers.
+// checks, workspace sizing, dispatch to the per-precision drivers, the split
+// of a batch over two internal streams (and its opt-in autotuner), and the
+// launch counter and per-kernel profiler.  The Newton drivers, the bicomplex
+// inverse, the uneven-batch driver, the mixed precisions and the tensor-core
+// GEMM have their entry points in newton.cu, iqe.cu, batched.cu, mixed.cu /
+// api (dispatch) and tc_gemm.cu.
 #include <atomic>
 #include <map>
 #include <mutex>

@@ -1,5 +1,10 @@
 // Host-side drivers: the blocked factorisations and solves built from the
-// kernels of dense_impl.cuh, and the four inversion algorithms.
+// kernels of dense_impl.cuh (with the one-CTA FP32 factorisations for
+// n <= 512), the four inversion algorithms (Frobenius with LU, including the
+// formula for invertible B and the automatic choice of the factored part;
+// Frobenius with Cholesky; complex LU; complex Cholesky), the Frobenius
+// linear solve, the complex-LU and 2n real augmented solves, and the
+// adjoint.
 #pragma once
 
 #include <algorithm>
