@@ -49,7 +49,7 @@ def algorithmic_flops(n, batch):
         "gemm<f64,op0,op0,frob_out>": 2 * n3,     # X7 = X2 X6 (+ interleaved output)
         "trsm<f64,op0,lower>": n3,                # R1^T X1 = B
         "gemm<f64,op1,op0,axpby>": 4 * n3 / 3,    # S = A - X1^T X1 and X6 = X5^T X5 (k >= max(i, j)), lower tiles
-        "trsm<f64,op0,lower,rhs=I>": n3 / 3,      # R2^T X5 = I (X5 lower triangular)
+        "gemm<f64,op0,op0,axpby>": n3 / 3,        # X5 = L2^{-1}, recursive triangular inverse (joined pairs)
         "gemm<f64,op0,op2,axpby>": 2 * n3 / 3,    # trailing updates of the two Cholesky factorisations
     }
 

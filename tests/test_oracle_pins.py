@@ -376,3 +376,18 @@ def test_bicomplex_special_cases(oracle_lib):
     assert np.abs(y0 - np.linalg.inv(a)).max() <= 1e-12 * np.abs(np.linalg.inv(a)).max() and np.abs(y1).max() == 0.0
     y0, y1 = oracle.bicomplex_inv(z, a)
     assert np.abs(y0).max() <= 1e-13 and np.abs(y1 + np.linalg.inv(a)).max() <= 1e-12 * np.abs(np.linalg.inv(a)).max()
+
+
+def test_bench_flop_table_sums_to_the_executed_count():
+    """The benchmark's per-kernel algorithmic flops (the numerator of the
+    roofline's achieved rate) add up to the executed count of the
+    Frobenius-Cholesky step, 19 n^3 / 3 per matrix."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    n, batch = 512, 64
+    total = sum(bench.algorithmic_flops(n, batch).values())
+    assert abs(total - flops.executed("frob_chol", n) * batch) <= 1e-9 * total
