@@ -193,8 +193,10 @@ frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t 
  * and launch nothing.  Other argument errors return FROB_ERR_ARG.
  *
  * The first call made with a given device current looks up the scratch
- * array's device address on that device; make that first call before any
- * stream capture.  The function itself calls no cudaMalloc, cudaFree or other
+ * array's device address on that device and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not reset
+ * the device (cudaDeviceReset) between calls, since the array may move when
+ * the library's module is loaded again.  The function itself calls no cudaMalloc, cudaFree or other
  * allocating routine.  All calls share the one scratch array, which keeps
  * whatever the last call left in it (no call depends on its contents):
  * calls whose work overlaps on the GPU -- on different streams, or from

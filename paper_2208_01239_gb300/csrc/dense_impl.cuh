@@ -1280,4 +1280,238 @@ __global__ void __launch_bounds__(SLU_THREADS, 1) getrf_small_kernel(int n, MatB
   }
 }
 
+// ------------------------------------------------------------------ multi-CTA panel
+// LU with partial pivoting of one column panel [k0, k0 + kb) of a large
+// matrix by G cooperating CTAs (grid: G x batch, one cooperative launch), for
+// matrices too few to fill the GPU one CTA each.  CTA c keeps panel rows
+// [c R, c R + R) in shared memory; row j of the panel always lies in CTA 0
+// (R >= PANEL_MAX).  Per pivot column j, one grid-wide exchange:
+//   1. every CTA finds its local candidate (largest key, lowest row) and
+//      publishes it with a copy of that row; CTA 0 also publishes row j;
+//   2. a grid barrier (bounded wait);
+//   3. every CTA reduces the G candidates in the same order (the same pivot
+//      as the one-CTA kernels: largest key, ties to the lowest row, NaN
+//      never wins), the owner of row j takes the pivot row, the owner of the
+//      pivot row takes the old row j, and every CTA scales and updates its
+//      rows below j with the pivot row.
+// The candidates are double-buffered by the parity of j, so one barrier per
+// column suffices: a CTA can only overwrite buffer j mod 2 after every CTA
+// has passed the barrier of column j + 1, i.e. has finished reading it.
+// Arithmetic per element is that of getrf_panel_kernel (the same scaling by
+// the reciprocal pivot and the same fused updates), so the factors are
+// identical.  A wait that gives up sets the per-matrix flag, reports
+// FROB_ERR_TIMEOUT and skips every later wait of the call; the results are
+// then unusable but no CTA hangs.
+constexpr int MC_THREADS = 256;
+constexpr int MC_GMAX = 256;         // cooperating CTAs per matrix, at most
+constexpr int MC_MIN_ROWS = 128;     // rows per CTA, at least
+constexpr int MC_BATCH_MAX = 16;     // matrices per call that take this path
+constexpr size_t MC_SMEM_MAX = 200 * 1024;
+
+template <typename K> struct McKey {
+  K key;
+  int idx;
+  int bad;
+};
+struct McHdr {
+  unsigned count, gen;
+  int err, pad;
+};
+// per-matrix scratch: header | keys[2][MC_GMAX] | rows[2][MC_GMAX][PANEL_MAX] | jrow[2][PANEL_MAX]
+template <typename T> constexpr size_t mc_keys_off() { return 256; }
+template <typename T> constexpr size_t mc_rows_off() {
+  return mc_keys_off<T>() + ((2 * MC_GMAX * sizeof(McKey<typename real_of<T>::type>) + 255) & ~(size_t)255);
+}
+template <typename T> constexpr size_t mc_jrow_off() {
+  return mc_rows_off<T>() + ((2 * MC_GMAX * PANEL_MAX * sizeof(T) + 255) & ~(size_t)255);
+}
+template <typename T> constexpr size_t mc_scratch_per_matrix() {
+  return mc_jrow_off<T>() + ((2 * PANEL_MAX * sizeof(T) + 255) & ~(size_t)255);
+}
+
+// loads through L2 (not L1, which is not coherent across SMs) of values
+// another CTA wrote
+__device__ __forceinline__ double ldcg_(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ zd ldcg_(const zd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return zd{v.x, v.y};
+}
+__device__ __forceinline__ zf ldcg_(const zf* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return zf{v.x, v.y};
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of the G CTAs of one matrix (sense by generation count).  Returns
+// true when this or an earlier wait of the call gave up.
+__device__ __forceinline__ bool mc_barrier(McHdr* h, unsigned G, long long limit_cycles) {
+  __shared__ int s_gaveup;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int gaveup = *reinterpret_cast<volatile int*>(&h->err);
+    if (!gaveup) {
+      const unsigned g = ld_acquire_u32(&h->gen);
+      __threadfence();
+      const unsigned arrived = atomicAdd(&h->count, 1u) + 1u;
+      if (arrived == G) {
+        atomicExch(&h->count, 0u);
+        __threadfence();
+        atomicAdd(&h->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&h->gen) == g) {
+          if (clock64() - t0 > limit_cycles) {
+            atomicExch(&h->err, 1);
+            gaveup = 1;
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __threadfence();
+    }
+    s_gaveup = gaveup;
+  }
+  __syncthreads();
+  return s_gaveup != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k0, int kb, MatB<T> A, int* piv,
+                                                                     frob_info* info, int info_off,
+                                                                     unsigned char* scr, int64_t scr_bs, int R,
+                                                                     long long limit_cycles) {
+  using K = typename real_of<T>::type;
+  constexpr int PS = PANEL_MAX + 1;
+  const int b = blockIdx.y, c = blockIdx.x, G = gridDim.x, t = threadIdx.x;
+  const int m = n - k0;
+  const int row0 = c * R;
+  const int rc = max(0, min(R, m - row0));
+  unsigned char* s = scr + (int64_t)b * scr_bs;
+  McHdr* hdr = reinterpret_cast<McHdr*>(s);
+  McKey<K>* keys = reinterpret_cast<McKey<K>*>(s + mc_keys_off<T>());
+  T* rows = reinterpret_cast<T*>(s + mc_rows_off<T>());
+  T* jrow = reinterpret_cast<T*>(s + mc_jrow_off<T>());
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);
+  __shared__ KeyIdx<K> red[MC_THREADS / 32];
+  __shared__ int redbad[MC_THREADS / 32];
+  __shared__ T pr[PANEL_MAX];
+  __shared__ T s_rinv;
+  __shared__ int s_lwin, s_win, s_p, s_ok;
+  T* g = A.at(b) + (int64_t)(k0 + row0) * A.ld + k0;
+  for (int e = t; e < rc * kb; e += MC_THREADS) P[(e / kb) * PS + (e % kb)] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const int par = j & 1;
+    // 1. local candidate over the rows >= j of column j
+    KeyIdx<K> best{(K)-1, 0x7fffffff};
+    bool bad = false;
+    for (int lr = t; lr < rc; lr += MC_THREADS) {
+      const int gi = row0 + lr;
+      if (gi >= j) {
+        const K kv = pkey(P[lr * PS + j]);
+        if (!(kv == kv) || kv == (K)INFINITY) bad = true;
+        best = kmax(best, KeyIdx<K>{kv, gi});
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, best.key, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+      best = kmax(best, other);
+    }
+    const unsigned wbad = __ballot_sync(0xffffffffu, bad);
+    if ((t & 31) == 0) {
+      red[t >> 5] = best;
+      redbad[t >> 5] = wbad != 0;
+    }
+    __syncthreads();
+    if (t == 0) {
+      KeyIdx<K> bb = red[0];
+      int anybad = redbad[0];
+      for (int w = 1; w < MC_THREADS / 32; ++w) {
+        bb = kmax(bb, red[w]);
+        anybad |= redbad[w];
+      }
+      McKey<K> kk;
+      kk.key = bb.key;
+      kk.idx = bb.idx;
+      kk.bad = anybad;
+      keys[par * MC_GMAX + c] = kk;
+      s_lwin = bb.idx;
+    }
+    __syncthreads();
+    if (t < kb) {
+      if (s_lwin != 0x7fffffff) rows[((int64_t)par * MC_GMAX + c) * PANEL_MAX + t] = P[(s_lwin - row0) * PS + t];
+      if (c == 0) jrow[par * PANEL_MAX + t] = P[j * PS + t];
+    }
+    // 2. grid barrier
+    if (mc_barrier(hdr, (unsigned)G, limit_cycles)) {
+      if (c == 0 && t == 0) report(info, b, FROB_ERR_TIMEOUT, info_off + k0 + j + 1);
+      break;
+    }
+    // 3. the pivot, the same in every CTA (candidates reduced in CTA order);
+    // its row was published by the CTA that owns it, p / R
+    if (t < 32) {
+      KeyIdx<K> bb{(K)-1, 0x7fffffff};
+      int anybad = 0;
+      for (int q = t; q < G; q += 32) {
+        const McKey<K>* kp = keys + par * MC_GMAX + q;
+        anybad |= __ldcg(&kp->bad);
+        bb = kmax(bb, KeyIdx<K>{__ldcg(&kp->key), __ldcg(&kp->idx)});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, bb.key, o), __shfl_xor_sync(0xffffffffu, bb.idx, o)};
+        bb = kmax(bb, other);
+      }
+      anybad = __any_sync(0xffffffffu, anybad);
+      if (t == 0) {
+        const bool none = bb.idx == 0x7fffffff;
+        s_p = none ? j : bb.idx;
+        s_win = none ? -1 : bb.idx / R;
+        s_ok = !anybad && bb.key > (K)0;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (t < kb) pr[t] = s_win >= 0 ? ldcg_(&rows[((int64_t)par * MC_GMAX + s_win) * PANEL_MAX + t]) : P[j * PS + t];
+    __syncthreads();
+    if (p != j && t < kb) {
+      if (c == 0) P[j * PS + t] = pr[t];
+      if (p >= row0 && p < row0 + rc) P[(p - row0) * PS + t] = ldcg_(&jrow[par * PANEL_MAX + t]);
+    }
+    if (t == 0) {
+      if (c == 0) {
+        piv[(int64_t)b * n + k0 + j] = k0 + p;
+        if (!s_ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+      }
+      s_rinv = s_ok ? recip_(pr[j]) : one_v<T>();
+    }
+    __syncthreads();
+    // scale column j below the pivot, then the rank-1 update of the rest
+    if (s_ok) {
+      const T rinv = s_rinv;
+      for (int lr = t; lr < rc; lr += MC_THREADS)
+        if (row0 + lr > j) P[lr * PS + j] = mul_(P[lr * PS + j], rinv);
+    }
+    __syncthreads();
+    const int w = kb - j - 1;
+    if (w > 0)
+      for (int e = t; e < rc * w; e += MC_THREADS) {
+        const int lr = e / w, cc = j + 1 + e % w;
+        if (row0 + lr > j) mac(P[lr * PS + cc], neg_(P[lr * PS + j]), pr[cc]);
+      }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int e = t; e < rc * kb; e += MC_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[(e / kb) * PS + (e % kb)];
+}
+
 }  // namespace frob

@@ -74,6 +74,10 @@ extern "C" frob_status frob_inv_hpd_noalloc(int n, int batch, const void* M, int
   void* ws = nullptr;
   frob_status s = scratch_on_current_device(&ws);
   if (s != FROB_OK) return s;
+  // An error left pending by an earlier runtime call of this thread is not
+  // this call's: clear it so that the check after the launches sees only
+  // their own status (a sticky error would make the launches fail anyway).
+  (void)cudaGetLastError();
   // Every scratch byte the kernels read is first written by this same call
   // (the split writes A, S and B; the identity solve writes every tile of
   // its output, zeros included), so nothing has to be cleared between calls.

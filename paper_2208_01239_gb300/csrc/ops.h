@@ -19,11 +19,13 @@ template <typename R> struct Planes {
   int *piv1, *piv2, *rp1, *rp2;
   int* partb;         // [batch] 1: B factored (frob_lu_run)
   frob_info* infoB;   // [batch] status of the LU of B (FROB_PART_AUTO)
+  unsigned char* mcs = nullptr;  // scratch of the multi-CTA LU panels (0 bytes when unused)
 };
 // Workspace of the complex baselines.
 template <typename C> struct CPlanes {
   MatB<C> W, Y;
   int *piv, *rp;
+  unsigned char* mcs = nullptr;  // scratch of the multi-CTA LU panels (0 bytes when unused)
 };
 
 template <typename R> size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out);

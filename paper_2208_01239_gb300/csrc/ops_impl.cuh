@@ -196,6 +196,71 @@ inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm,
   }
 }
 
+// X[r] = B[rp[r]] (rp NULL: a plain copy), n rows of ncols entries
+template <typename T>
+__global__ void rowgather_kernel(int n, int ncols, MatB<const T> B, MatB<T> X, const int* rp) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * ncols) return;
+  const int r = (int)(e / ncols), c = (int)(e % ncols);
+  const int sr = rp ? rp[(int64_t)b * n + r] : r;
+  X.at(b)[(int64_t)r * X.ld + c] = B.at(b)[(int64_t)sr * B.ld + c];
+}
+
+// Recursive triangular solve op(T) X = X in place (Elmroth, Gustavson,
+// Jonsson and Kagstrom's recursive blocking): split at h, solve the first
+// half, remove its contribution from the second half with one product,
+// solve the second half.  Almost all of the n^2 nrhs flops land in large
+// products that spread over the whole GPU, where the block-row steps of
+// trsm() have only ceil(nrhs / 64) x batch CTAs each; blocks of at most
+// TRSM_REC_BASE rows use trsm().
+constexpr int TRSM_REC_BASE = 256;
+constexpr int TRSM_REC_MIN = 1024;   // smallest order that takes the recursive form
+constexpr int TRSM_REC_TILES = 512;  // ... when ceil(nrhs / 64) x batch is at most this
+
+template <typename T, int OPT, bool LOWER, bool UNIT>
+inline void trsm_rec(int n, int nrhs, int batch, MatB<const T> Tm, MatB<T> X, cudaStream_t st) {
+  if (n <= TRSM_REC_BASE) {
+    trsm<T, OPT, LOWER, UNIT, false>(n, nrhs, batch, Tm, MatB<const T>{X.p, X.ld, X.bs}, X, nullptr, st);
+    return;
+  }
+  const int h = ((n / 2 + TB - 1) / TB) * TB;
+  // block (i0, j0) of op(T) as a GEMM operand of mode OPT
+  auto blk = [&](int i0, int j0) { return OPT == OP_N ? Tm.sub(i0, j0) : Tm.sub(j0, i0); };
+  auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
+  if (LOWER) {
+    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st);
+    gemm_launch<T, OPT, OP_N>(n - h, nrhs, h, batch, blk(h, 0), cst(X), axpby<T>(X.sub(h, 0), neg_(one_v<T>()),
+                                                                                 one_v<T>(), false), 0, st);
+    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st);
+  } else {
+    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st);
+    gemm_launch<T, OPT, OP_N>(h, nrhs, n - h, batch, blk(0, h), cst(X.sub(h, 0)),
+                              axpby<T>(X, neg_(one_v<T>()), one_v<T>(), false), 0, st);
+    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st);
+  }
+}
+
+// op(T) X = P B (rowperm) or = B: the recursive form for large orders with
+// few right-hand-side tiles, else the block-row steps.  X may alias B when
+// rowperm is NULL.
+template <typename T, int OPT, bool LOWER, bool UNIT>
+inline void trsm_any(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm, MatB<T> X, const int* rowperm,
+                     cudaStream_t st) {
+  const int64_t tiles = (int64_t)((nrhs + TB - 1) / TB) * batch;
+  if (n < TRSM_REC_MIN || tiles > TRSM_REC_TILES) {
+    trsm<T, OPT, LOWER, UNIT, false>(n, nrhs, batch, Tm, Bm, X, rowperm, st);
+    return;
+  }
+  if (rowperm || Bm.p != X.p) {
+    const int64_t ne = (int64_t)n * nrhs;
+    FROB_LAUNCH("rowgather", st,
+                rowgather_kernel<T><<<dim3((unsigned)((ne + 255) / 256), 1, (unsigned)batch), 256, 0, st>>>(
+                    n, nrhs, Bm, X, rowperm));
+  }
+  trsm_rec<T, OPT, LOWER, UNIT>(n, nrhs, batch, Tm, X, st);
+}
+
 // X = L^{-1} for lower triangular L (unit diagonal if UNIT), recursively:
 // the 64 x 64 diagonal blocks are inverted in one launch, then neighbouring
 // blocks of size s = 64, 128, ... are joined,
@@ -243,9 +308,34 @@ template <typename T> inline const char* laswp_name() {
   static const std::string s = std::string("laswp_trsm<") + type_tag<T>() + ">";
   return s.c_str();
 }
+// Scratch of the multi-CTA panel factorization (getrf_panel_mc_kernel), carved
+// from the caller's workspace by the routines that factor with getrf: used for
+// matrices of order above PANEL_THREADS in calls of at most MC_BATCH_MAX
+// matrices, 0 bytes otherwise.
+template <typename T> inline size_t mc_scratch_bytes(int n, int batch) {
+  return (n > PANEL_THREADS && batch <= MC_BATCH_MAX) ? mc_scratch_per_matrix<T>() * (size_t)batch : 0;
+}
+
+inline int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+template <typename T> inline const char* getrf_mc_name() {
+  static const std::string s = std::string("getrf_panel_mc<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+
 // Blocked right-looking LU with partial pivoting (P A = L U, in place).
+// Panels of more than PANEL_THREADS rows are factored by several cooperating
+// CTAs per matrix when `mcs` (mc_scratch_bytes of scratch) is given: one
+// cooperative launch of G x batch CTAs, G x batch at most one per SM, so a
+// single large matrix keeps the panel off its critical path's single SM.
 template <typename T>
-inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st) {
+inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
+                  unsigned char* mcs = nullptr) {
   if constexpr (std::is_same<T, float>::value) {
     if (n <= SLU_MAX) {
       // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
@@ -256,18 +346,41 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
     }
   }
   panel_smem_attr<T>();
+  const bool mc = mcs != nullptr && mc_scratch_bytes<T>(n, batch) > 0;
+  const int gcap = mc ? std::max(1, std::min(MC_GMAX, num_sms() / batch)) : 0;
+  if (mc) {
+    set_smem_attr(getrf_panel_mc_kernel<T>, (int)MC_SMEM_MAX);
+    cudaMemsetAsync(mcs, 0, mc_scratch_bytes<T>(n, batch), st);  // barrier counters and flags
+  }
   const int nb = panel_width<T>();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
-    const size_t bytes = (size_t)(n - k0) * (kb + 1) * sizeof(T);
+    const int m = n - k0;
+    const size_t bytes = (size_t)m * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
-    if (n - k0 <= PANEL_THREADS && sizeof(T) <= 8)
+    int R = 0, G = 0;
+    if (mc && m > PANEL_THREADS) {
+      R = std::max(MC_MIN_ROWS, (m + gcap - 1) / gcap);
+      G = (m + R - 1) / R;
+      if ((size_t)R * (PANEL_MAX + 1) * sizeof(T) > MC_SMEM_MAX) G = 0;
+    }
+    if (G > 0) {
+      const size_t smem = (size_t)R * (PANEL_MAX + 1) * sizeof(T);
+      int64_t bs = (int64_t)mc_scratch_per_matrix<T>();
+      long long limit = 1ll << 31;  // about a second of SM clock
+      void* args[] = {(void*)&n, (void*)&k0, (void*)&kb, (void*)&A, (void*)&piv, (void*)&info, (void*)&info_off,
+                      (void*)&mcs, (void*)&bs, (void*)&R, (void*)&limit};
+      FROB_LAUNCH(getrf_mc_name<T>(), st,
+                  cudaLaunchCooperativeKernel((const void*)getrf_panel_mc_kernel<T>, dim3((unsigned)G, (unsigned)batch),
+                                              dim3(MC_THREADS), args, smem, st));
+    } else if (m <= PANEL_THREADS && sizeof(T) <= 8) {
       FROB_LAUNCH(getrf_panel_name<T>(), st,
                   getrf_panel_reg_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(n, k0, kb, A, piv, info, info_off));
-    else
+    } else {
       FROB_LAUNCH(getrf_panel_name<T>(), st,
                   getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info,
                                                                                          info_off, staged));
+    }
     FROB_LAUNCH(laswp_name<T>(), st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
     const int r = k0 + kb;
     if (r < n) {
@@ -357,6 +470,7 @@ size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.rp2 = c.take<int>((size_t)n * batch);
   p.partb = c.take<int>((size_t)batch);
   p.infoB = c.take<frob_info>((size_t)batch);
+  p.mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n, batch));
   if (out) *out = p;
   return c.off;
 }
@@ -438,25 +552,25 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
                                                        o.attempt, o.part == FROB_PART_B ? 1 : 0,
                                                        autop ? p.X1 : MatB<R>{nullptr, 0, 0}, p.partb,
                                                        autop ? p.infoB : nullptr));
-  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                       // A = P1^T L1 U1
+  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st, p.mcs);                                // A = P1^T L1 U1
   if (autop) {
     // the LU of B in the X1 plane (free until the first solve), its pivots
     // in rp1 (free until the row map is built); keep the better-conditioned
-    getrf<R>(n, batch, p.X1, p.rp1, p.infoB, 0, st);
+    getrf<R>(n, batch, p.X1, p.rp1, p.infoB, 0, st, p.mcs);
     FROB_LAUNCH("choose_part", st,
                 choose_part_kernel<R><<<batch, 256, 0, st>>>(n, cst(p.LA), cst(p.X1), info, p.infoB, p.partb));
     FROB_LAUNCH("swap_part", st, swap_part_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(
                                      n, p.partb, p.LA, cst(p.X1), p.S, p.Bp, p.piv1, p.rp1, info));
   }
   rowperm(n, batch, p.piv1, p.rp1, st);
-  trsm<R, OP_N, true, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);   // L1 Y = P1 B
-  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st); // U1 X1 = Y
+  trsm_any<R, OP_N, true, true>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);   // L1 Y = P1 B
+  trsm_any<R, OP_N, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st); // U1 X1 = Y
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.X1), axpby<R>(p.S, (R)1, (R)1, false), 0,
                              st);                                                       // S = A + B X1
-  getrf<R>(n, batch, p.S, p.piv2, info, n, st);                                        // S = P2^T L2 U2
+  getrf<R>(n, batch, p.S, p.piv2, info, n, st, p.mcs);                                 // S = P2^T L2 U2
   rowperm(n, batch, p.piv2, p.rp2, st);
   trtri<R, true>(n, batch, cst(p.S), p.Y, p.LA, st);                                     // Y = L2^{-1}
-  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
+  trsm_any<R, OP_N, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
   EpiFrobOut<R> epi{X, cst(p.Y), p.rp2, n, o.almost_sure ? info : nullptr,
                     o.part != FROB_PART_A ? p.partb : nullptr};
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.X1), cst(p.Y), epi, 0, st);          // X = Z P2 - i X1 Z P2
@@ -483,10 +597,10 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
   potrf<R>(n, batch, p.LA, info, 0, st);                                                 // A = R1^T R1, L1 = R1^T
-  trsm<R, OP_N, true, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X1 = L1^{-1} B
+  trsm_any<R, OP_N, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X1 = L1^{-1} B
   gemm_launch<R, OP_T, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.Bp), axpby<R>(p.S, (R)-1, (R)1, false), 1,
                              st);                                                         // S = A - X1^T X1
-  trsm<R, OP_T, false, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X2 = L1^{-T} X1
+  trsm_any<R, OP_T, false, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.Bp, nullptr, st); // X2 = L1^{-T} X1
   potrf<R>(n, batch, p.S, info, n, st);                                                  // S = R2^T R2
   trtri<R, false>(n, batch, cst(p.S), p.Y, p.LA, st);                                    // X5 = L2^{-1}
   // X6 = L2^{-T} X5 = X5^T X5 (S^{-1} = L2^{-T} L2^{-1}): a product of the
@@ -513,6 +627,7 @@ size_t cplx_lu_ws(int n, int batch, void* ws, CPlanes<C>* out) {
   p.Y = plane<C>(c, n, batch);
   p.piv = c.take<int>((size_t)n * batch);
   p.rp = c.take<int>((size_t)n * batch);
+  p.mcs = c.take<unsigned char>(mc_scratch_bytes<C>(n, batch));
   if (out) *out = p;
   return c.off;
 }
@@ -523,10 +638,10 @@ void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_in
   cplx_lu_ws<C>(n, batch, ws, &p);
   auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.W, info));
-  getrf<C>(n, batch, p.W, p.piv, info, 0, st);                                           // M = P^T L U
+  getrf<C>(n, batch, p.W, p.piv, info, 0, st, p.mcs);                                    // M = P^T L U
   rowperm(n, batch, p.piv, p.rp, st);
   trtri<C, true>(n, batch, cst(p.W), p.Y, X, st);                                         // Y = L^{-1}
-  trsm<C, OP_N, false, false, false>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);  // Z = U^{-1} Y
+  trsm_any<C, OP_N, false, false>(n, n, batch, cst(p.W), cst(p.Y), p.Y, nullptr, st);  // Z = U^{-1} Y
   FROB_LAUNCH("colperm", st, colperm_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(p.Y), X, p.rp));          // X = Z P
 }
 
@@ -597,6 +712,7 @@ inline dim3 rect_grid(int n, int m, int batch) {
 template <typename R> struct SolvePlanes {
   MatB<R> LA, S, Bp, X1, CD, T, U;
   int *piv1, *piv2, *rp1, *rp2;
+  unsigned char* mcs;
 };
 
 template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlanes<R>* out, void* ws) {
@@ -617,6 +733,7 @@ template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlan
   p.piv2 = c.take<int>((size_t)n * batch);
   p.rp1 = c.take<int>((size_t)n * batch);
   p.rp2 = c.take<int>((size_t)n * batch);
+  p.mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n, batch));
   if (out) *out = p;
   return c.off;
 }
@@ -630,23 +747,23 @@ void frob_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   const int m2 = 2 * nrhs;
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, 0, 0, 0));
-  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st);                                              // step 1
+  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st, p.mcs);                                       // step 1
   rowperm(n, batch, p.piv1, p.rp1, st);
-  trsm<R, OP_N, true, true, false>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);          // step 2
-  trsm<R, OP_N, false, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st);
+  trsm_any<R, OP_N, true, true>(n, n, batch, cst(p.LA), cst(p.Bp), p.X1, p.rp1, st);          // step 2
+  trsm_any<R, OP_N, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st);
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.X1), axpby<R>(p.S, (R)1, (R)1, false), 0, st);  // 3
-  getrf<R>(n, batch, p.S, p.piv2, info, n, st);                                               // step 4
+  getrf<R>(n, batch, p.S, p.piv2, info, n, st, p.mcs);                                        // step 4
   rowperm(n, batch, p.piv2, p.rp2, st);
   FROB_LAUNCH("rhs_split", st, rhs_split_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, Bc, p.CD));
-  trsm<R, OP_N, true, true, false>(n, m2, batch, cst(p.S), cst(p.CD), p.T, p.rp2, st);          // step 5
-  trsm<R, OP_N, false, false, false>(n, m2, batch, cst(p.S), cst(p.T), p.T, nullptr, st);     // T = [x1 | y1]
+  trsm_any<R, OP_N, true, true>(n, m2, batch, cst(p.S), cst(p.CD), p.T, p.rp2, st);          // step 5
+  trsm_any<R, OP_N, false, false>(n, m2, batch, cst(p.S), cst(p.T), p.T, nullptr, st);     // T = [x1 | y1]
   // step 6: CD = B [y1 | x1], then U = A^{-1} CD = [x2 | y2]
   MatB<const R> Ty{p.T.p + nrhs, p.T.ld, p.T.bs}, Tx{p.T.p, p.T.ld, p.T.bs};
   gemm_launch<R, OP_N, OP_N>(n, nrhs, n, batch, cst(p.Bp), Ty, axpby<R>(p.CD, (R)1, (R)0, true), 0, st);
   gemm_launch<R, OP_N, OP_N>(n, nrhs, n, batch, cst(p.Bp), Tx,
                              axpby<R>(MatB<R>{p.CD.p + nrhs, p.CD.ld, p.CD.bs}, (R)1, (R)0, true), 0, st);
-  trsm<R, OP_N, true, true, false>(n, m2, batch, cst(p.LA), cst(p.CD), p.U, p.rp1, st);
-  trsm<R, OP_N, false, false, false>(n, m2, batch, cst(p.LA), cst(p.U), p.U, nullptr, st);
+  trsm_any<R, OP_N, true, true>(n, m2, batch, cst(p.LA), cst(p.CD), p.U, p.rp1, st);
+  trsm_any<R, OP_N, false, false>(n, m2, batch, cst(p.LA), cst(p.U), p.U, nullptr, st);
   FROB_LAUNCH("solve_out", st,
               solve_out_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, cst(p.T), cst(p.U), X));  // 7
 }
@@ -658,6 +775,7 @@ template <typename C> size_t cplx_solve_ws(int n, int nrhs, int batch) {
   c.take<C>((size_t)n * nrhs * batch);
   c.take<int>((size_t)n * batch);
   c.take<int>((size_t)n * batch);
+  c.take<unsigned char>(mc_scratch_bytes<C>(n, batch));
   return c.off;
 }
 
@@ -669,13 +787,14 @@ void cplx_solve_run(int n, int nrhs, int batch, MatB<const C> M, MatB<const C> B
   C* yp = c.take<C>((size_t)n * nrhs * batch);
   int* piv = c.take<int>((size_t)n * batch);
   int* rp = c.take<int>((size_t)n * batch);
+  unsigned char* mcs = c.take<unsigned char>(mc_scratch_bytes<C>(n, batch));
   MatB<C> Y{yp, nrhs, (int64_t)n * nrhs};
   auto cst = [](MatB<C> m) { return MatB<const C>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("copy", st, copy_kernel<C><<<elem_grid(n, batch), 256, 0, st>>>(n, M, W, info));
-  getrf<C>(n, batch, W, piv, info, 0, st);
+  getrf<C>(n, batch, W, piv, info, 0, st, mcs);
   rowperm(n, batch, piv, rp, st);
-  trsm<C, OP_N, true, true, false>(n, nrhs, batch, cst(W), Bc, Y, rp, st);
-  trsm<C, OP_N, false, false, false>(n, nrhs, batch, cst(W), cst(Y), X, nullptr, st);
+  trsm_any<C, OP_N, true, true>(n, nrhs, batch, cst(W), Bc, Y, rp, st);
+  trsm_any<C, OP_N, false, false>(n, nrhs, batch, cst(W), cst(Y), X, nullptr, st);
 }
 
 // The 2n real augmented system (the third linear-solve method of Sec. 5.2):
@@ -728,6 +847,7 @@ template <typename R> size_t aug_solve_ws(int n, int nrhs, int batch) {
   c.take<R>((size_t)2 * n * nrhs * batch);
   c.take<int>((size_t)2 * n * batch);
   c.take<int>((size_t)2 * n * batch);
+  c.take<unsigned char>(mc_scratch_bytes<R>(2 * n, batch));
   return c.off;
 }
 
@@ -742,14 +862,15 @@ void aug_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::t
   R* xyp = c.take<R>((size_t)n2 * nrhs * batch);
   int* piv = c.take<int>((size_t)n2 * batch);
   int* rp = c.take<int>((size_t)n2 * batch);
+  unsigned char* mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n2, batch));
   MatB<R> CD{cdp, nrhs, (int64_t)n2 * nrhs}, XY{xyp, nrhs, (int64_t)n2 * nrhs};
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("aug_build", st, aug_build_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, W));
   FROB_LAUNCH("aug_rhs", st, aug_rhs_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, Bc, CD, info));
-  getrf<R>(n2, batch, W, piv, info, 0, st);
+  getrf<R>(n2, batch, W, piv, info, 0, st, mcs);
   rowperm(n2, batch, piv, rp, st);
-  trsm<R, OP_N, true, true, false>(n2, nrhs, batch, cst(W), cst(CD), XY, rp, st);
-  trsm<R, OP_N, false, false, false>(n2, nrhs, batch, cst(W), cst(XY), XY, nullptr, st);
+  trsm_any<R, OP_N, true, true>(n2, nrhs, batch, cst(W), cst(CD), XY, rp, st);
+  trsm_any<R, OP_N, false, false>(n2, nrhs, batch, cst(W), cst(XY), XY, nullptr, st);
   FROB_LAUNCH("aug_out", st, aug_out_kernel<R><<<rect_grid(n, nrhs, batch), 256, 0, st>>>(n, nrhs, cst(XY), X));
 }
 

@@ -89,6 +89,84 @@ def test_frob_inv_fp32_vs_oracle(F, n):
             assert metrics.residual_fro(m64, got) <= RES_GATE["fp32"]
 
 
+# ------------------------------------------------------------------ large single matrices
+# Orders above 512 in calls of at most 16 matrices factor their panels with
+# several cooperating CTAs per matrix, and orders from 1024 on with few
+# right-hand-side tiles solve recursively; the sizes below cross both
+# thresholds with ragged tails (520 = 8 x 64 + 8, 777, 1030 = 16 x 64 + 6).
+
+
+@pytest.mark.parametrize("n", [520, 777, 1030])
+def test_large_orders_vs_oracle(F, n):
+    m = W.gaussian(n, 1, seed=5000 + n)[0]
+    ref = oracle.cplx_lu_inv(m)
+    for f in (F.frob_inv, F.cplx_lu_inv):
+        x = f(_dev(m)).x.cpu().numpy()
+        assert metrics.forward_error(x, ref) <= _fe_bound(m, "fp64")
+        assert metrics.residual_fro(m, x) <= RES_GATE["fp64"]
+
+
+def test_large_order_hpd_vs_closed_form(F):
+    """Cholesky route at n = 1030 (recursive solves with L and L^T)."""
+    n = 1030
+    ms, qs, lams = W.hpd(n, batch=1, seed=5100, return_parts=True)
+    exact = W.hpd_exact_inverse(qs[0], lams[0])
+    kappa = lams[0].max() / lams[0].min()
+    for f in (F.frob_inv_hpd, F.cplx_chol_inv):
+        x = f(_dev(ms)).x.cpu().numpy()[0]
+        assert metrics.forward_error(x, exact) <= 32 * n * kappa * U["fp64"]
+        assert metrics.residual_fro(ms[0], x) <= 1e-15
+
+
+def test_multi_cta_panel_matches_one_cta_panel_bitwise(F):
+    """The multi-CTA panel factorization chooses the same pivots and rounds
+    every entry the same way as the one-CTA panel kernels: a matrix inverted
+    alone (multi-CTA panels) equals the same matrix inverted inside a batch
+    of 34 (two slices of 17, beyond the multi-CTA limit of 16 per call),
+    bit for bit, for both routes and both precisions.  n = 600 stays below
+    the order of the recursive solves, so only the panels differ."""
+    n = 600
+    m = W.gaussian(n, 1, seed=5200)[0]
+    for prec in ("fp64", "fp32"):
+        dm = _dev(m, prec)
+        many = dm.unsqueeze(0).repeat(34, 1, 1).contiguous()
+        for f in (F.frob_inv, F.cplx_lu_inv):
+            one = f(dm, prec=prec).x
+            batch = f(many, prec=prec).x
+            assert torch.equal(one, batch[0]), (f.__name__, prec)
+            assert torch.equal(batch[0], batch[33]), (f.__name__, prec)
+
+
+def test_large_order_fp32_and_solve(F):
+    """FP32 at n = 1030 on the differentiation workload's distribution (A, B
+    iid N(0, 1) / sqrt(n) + 2I, the FP32 configuration the targets name)
+    against the oracle's inverse of the rounded input, and the Frobenius
+    linear solve at n = 1030 (both LU factorizations and the recursive solves
+    with two right-hand sides).  On a plain Gaussian matrix of this order the
+    FP32 Frobenius route's residual follows kappa(A) kappa(S) and exceeds
+    1e-5 (6e-5 measured), as the CPU route's would."""
+    n = 1030
+    m = W.sign_workload(n, batch=1, seed=5300)[0][0].astype(np.complex64)
+    m64 = m.astype(np.complex128)
+    ref = oracle.cplx_lu_inv(m64)
+    for f in (F.frob_inv, F.cplx_lu_inv):
+        x = f(_dev(m, "fp32"), prec="fp32").x.cpu().numpy().astype(np.complex128)
+        assert metrics.forward_error(x, ref) <= _fe_bound(m64, "fp32")
+        assert metrics.residual_fro(m64, x) <= RES_GATE["fp32"]
+    g = np.random.default_rng(5301)
+    m = W.gaussian(n, 1, seed=5302)[0]
+    xt = g.standard_normal((n, 2)) + 1j * g.standard_normal((n, 2))
+    rhs = m @ xt
+    # each route against the same route on the CPU: the Frobenius solve's
+    # error follows kappa(A) and kappa(S), not only kappa(M)
+    fe_cpu = {"frob_solve": np.abs(oracle.frob_solve(m, rhs) - xt).max() / np.abs(xt).max(),
+              "cplx_lu_solve": np.abs(np.linalg.solve(m, rhs) - xt).max() / np.abs(xt).max()}
+    for f in (F.frob_solve, F.cplx_lu_solve):
+        x = f(_dev(m), _dev(rhs)).x.cpu().numpy()
+        fe = np.abs(x - xt).max() / np.abs(xt).max()
+        assert fe <= max(32 * n * np.linalg.cond(m) * U["fp64"], 10 * fe_cpu[f.__name__]), (f.__name__, fe)
+
+
 def test_frob_inv_matches_frobenius_oracle_stagewise(F):
     """Same algorithm on both sides: agreement with the oracle's Frobenius
     route is as tight as with the LU route."""

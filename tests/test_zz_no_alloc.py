@@ -5,8 +5,10 @@ caller without a device allocator).  The library supplies the workspace from
 a fixed scratch array; the caller passes only inputs, outputs and info.
 
 The test calls the entry point through the C ABI twice in a row, on
-different inputs, and compares each result with frob_inv_hpd's (which uses a
-caller-provided workspace) within the tolerance of the parity tests.  It
+different inputs, and checks each result two ways within the tolerance of
+the parity tests: against frob_inv_hpd's (which uses a caller-provided
+workspace), and against the closed-form inverse Q diag(1/lam) Q^H that the
+generator M = Q diag(lam) Q^H fixes, which no GPU code computes.  It
 builds and loads the library itself, so it passes alone in a fresh process as
 well as after the other tests.  This file is collected last on purpose.
 """
@@ -66,6 +68,8 @@ def test_noalloc_matches_frob_inv_hpd_twice(lib):
         for b in range(batch):
             kappa = lams[b].max() / lams[b].min()
             assert _fe(got[b], ref[b]) <= 32 * n * kappa * U64, f"call {call}, matrix {b}"
+            exact = W.hpd_exact_inverse(qs[b], lams[b])
+            assert _fe(got[b], exact) <= 32 * n * kappa * U64, f"call {call}, matrix {b} (closed form)"
 
 
 def test_noalloc_rejects_problems_beyond_the_scratch(lib):
