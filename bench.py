@@ -1,19 +1,32 @@
-"""Benchmark: Frobenius inversion of Hermitian positive definite matrices on
-one GB300, against the complex-Cholesky baseline on the same GPU.
+"""Benchmark: Frobenius inversion of one large ill-conditioned complex matrix
+on one GB300, against complex-LU inversion on the same GPU.
 
-Workload: batch 64 of complex FP64 n = 512 HPD matrices M = Q diag(lam) Q^H,
-Q from the QR of a complex Gaussian matrix, lam log-uniform on [1, 1e4]
-(seeded, synthetic).  One step = one frob_inv_hpd call over the whole batch
-(split, two Cholesky factorisations, four triangular solves, the symmetric
-product, the final product and the interleaved output; Sec. 4.3).
+Workload (the largest single-GPU configuration): one complex FP64 matrix of
+order 8192, M = A + iB with A = I and B = Q blockdiag([[0, -s], [s, 0]]) Q^T,
+Q a Haar-random orthogonal matrix (seed 3), s = 1 - 1e-6, so that
+cond(A) = cond(B) = 1 and cond(M) ~ 2e6 (Sec. 3, the construction where
+Frobenius inversion's parts are well conditioned).  One step = one frob_inv
+call (split, LU of A, X1 = A^{-1} B, S = A + B X1, LU of S, S^{-1}, the final
+product with the interleaved output; Sec. 4.1).  The exact inverse is
+(I - iB)/(1 - s^2), so every step's result is checked entry by entry.
 
-Metric: complex inversions per second (whole job), with TFLOP/s (executed and
-nominal 8 n^3) and the relative residual reported beside it.  The input batch
-(268 MB) is larger than L2 (129 MB), so no flush is needed between steps.
+Metric: complex inversions per second (whole job) and TFLOP/s (executed
+26 n^3 / 3 for Frobenius, 8 n^3 for complex LU; nominal 8 n^3), with the
+complex-LU inverse on the same GPU, at equal residual, beside it.  The input
+(1.07 GB) is larger than L2 (129 MB), so no flush is needed between steps.
+
+The line also carries the other configurations: n = 256 Gaussian (us per
+inversion), 64 x n = 512 HPD (Frobenius-Cholesky vs complex Cholesky, FP64
+and mixed precision with the refined complex control), n = 8192 in FP32,
+1024 uneven Gaussian matrices (mixed Frobenius vs the refined complex-LU
+control vs FP64 complex LU), and the differentiation workload (16 x n = 1024
+complex FP32, 10 Newton sign steps: FrobInv autograd vs torch.linalg.inv
+autograd, peak memory with and without checkpointing).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank runs its own batch (weak scaling) and rank
-0 prints one JSON line with the whole-job throughput.
+Under torchrun (N > 1) every rank inverts its own replica of the single
+matrix (replicas only: a single LU does not shard), and the uneven batch is
+partitioned across ranks by shard.partition; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -28,30 +41,19 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_ORDER = 512
-BATCH = 64
-SEED = 2
-WORKLOAD = "hpd_batch64_n512_fp64"
-METRIC = "complex inversions/s (Frobenius-Cholesky vs complex Cholesky), 1 GB300, equal residual"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s
-# DRAM bytes (read + write) of one launch of the final product with the
-# interleaving epilogue (32 matrices of order 512), from one ncu capture of
-# the current kernel: profiles/gemm_frobout_f64_hpd_b64_n512.md
-TRAFFIC_PER_LAUNCH = {"gemm<f64,op0,op0,frob_out>": 226.1e6}
-
-
-def algorithmic_flops(n, batch):
-    """Real flops each kernel family of frob_inv_hpd must do per call (Sec. 4.3,
-    Algorithm "Frobenius inversion with Cholesky decomposition")."""
-    n3 = float(n) ** 3 * batch
-    return {
-        "trsm<f64,op1,upper>": n3,                # R1 X2 = X1, n right-hand sides
-        "gemm<f64,op0,op0,frob_out>": 2 * n3,     # X7 = X2 X6 (+ interleaved output)
-        "trsm<f64,op0,lower>": n3,                # R1^T X1 = B
-        "gemm<f64,op1,op0,axpby>": 4 * n3 / 3,    # S = A - X1^T X1 and X6 = X5^T X5 (k >= max(i, j)), lower tiles
-        "gemm<f64,op0,op0,axpby>": n3 / 3,        # X5 = L2^{-1}, recursive triangular inverse (joined pairs)
-        "gemm<f64,op0,op2,axpby>": 2 * n3 / 3,    # trailing updates of the two Cholesky factorisations
-    }
+N_ORDER = 8192
+SEED = 3
+S_ROT = 1.0 - 1e-6
+WORKLOAD = "ill_conditioned_n8192_c128"
+METRIC = "complex inversions/s and TFLOP/s, Frobenius vs complex-LU on 1 GB300, equal residual"
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit
+# counts and the maximum SM clock); a DFMA microbenchmark on this GPU type
+# measured 1.19 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+FP64_DFMA_MEASURED_TFLOPS = 1.19
+# Reference arm and CPU baseline: the oracle's Frobenius inversion with LU on
+# the same construction at this smaller order, scaled to order N_ORDER by n^3
+CPU_SAMPLE_ORDER = 1024
 
 
 def _dist():
@@ -61,9 +63,60 @@ def _dist():
     return ws, rank, local
 
 
-def _gen_inputs(n, batch, seed):
+def _cpu_sample(budget_s: float, min_runs: int = 1):
+    """The oracle (plain C FP64, Frobenius inversion with LU, Sec. 4.1) on the
+    ill-conditioned construction at order CPU_SAMPLE_ORDER, repeated until
+    budget_s has passed; returns (seconds per inversion, runs, threads)."""
+    import oracle
     from paper_2208_01239_gb300 import workloads as W
-    return W.hpd(n, batch=batch, seed=seed, return_parts=True)
+    oracle.build()
+    m, _ = W.ill_conditioned(CPU_SAMPLE_ORDER, seed=SEED)
+    oracle.frob_inv_lu(m)  # warm-up
+    runs, t0 = 0, time.perf_counter()
+    while runs < min_runs or time.perf_counter() - t0 < budget_s:
+        oracle.frob_inv_lu(m)
+        runs += 1
+    dt = time.perf_counter() - t0
+    return dt / runs, runs, oracle.num_threads()
+
+
+def _cpu_rate(sec_per_inv_sample: float) -> float:
+    """Inversions/s at order N_ORDER implied by the sample (work ~ n^3)."""
+    return 1.0 / (sec_per_inv_sample * (N_ORDER / CPU_SAMPLE_ORDER) ** 3)
+
+
+def run_reference(args):
+    """The CPU oracle timed as it stands on the host cores: each step is one
+    oracle Frobenius inversion (plain C FP64, Sec. 4.1) of the same
+    construction at order CPU_SAMPLE_ORDER, and the rate is scaled to order
+    8192 by n^3."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2208_01239_gb300 import workloads as W
+    oracle.build()
+    m, _ = W.ill_conditioned(CPU_SAMPLE_ORDER, seed=SEED)
+    for _ in range(args.warmup):
+        oracle.frob_inv_lu(m)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.frob_inv_lu(m)
+    dt = time.perf_counter() - t0
+    value = _cpu_rate(dt / args.steps)
+    cores = oracle.num_threads()
+    sample = (f"one oracle frob_inv_lu (plain C FP64, OpenMP) of the same construction at n={CPU_SAMPLE_ORDER} "
+              f"per step, rate scaled to n={N_ORDER} by n^3 (x{(N_ORDER // CPU_SAMPLE_ORDER) ** 3})")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "inversions/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_ORDER, "sample_order": CPU_SAMPLE_ORDER, "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "inversions/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "inversions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def _clock_sampler():
@@ -105,39 +158,88 @@ def _clock_summary(proc, gpu_index):
             "samples": len(sm)}
 
 
-def run_reference(args):
-    """The CPU oracle (plain C FP64, Frobenius inversion with Cholesky,
-    Sec. 4.3) timed as it stands on the host cores, on a bounded sample of the
-    same workload per step."""
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return 0
-    import oracle
-    sample = 2
-    ms, _, _ = _gen_inputs(N_ORDER, sample, SEED)
-    oracle.build()
-    for _ in range(args.warmup):
-        for b in range(sample):
-            oracle.frob_inv_chol(ms[b])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for b in range(sample):
-            oracle.frob_inv_chol(ms[b])
-    dt = time.perf_counter() - t0
-    value = sample * args.steps / dt
-    cores = oracle.num_threads()
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "inversions/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_ORDER, "batch": BATCH, "sample_per_step": sample},
-        "cpu_baseline": {"value": value, "unit": "inversions/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} of the {BATCH} n={N_ORDER} HPD matrices per step, "
-                                   "oracle frob_inv_chol (plain C FP64, OpenMP)"},
-        "e2e": {"value": value, "unit": "inversions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+def _timed(fn, steps, stream, barrier):
+    """CUDA-event time of `steps` calls of fn on `stream`, barrier and
+    device synchronisation on both sides (ms, whole region)."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    barrier()
+    return ev0.elapsed_time(ev1)
+
+
+def _profile(frob, fn, steps, sync):
+    """Per-kernel-variant device time and algorithmic flops over `steps`
+    calls, from the library's event-bracketed launches (each kernel timed
+    alone): {name: (launches, ms, flops)} per step."""
+    frob.profile_enable(True)
+    for _ in range(steps):
+        fn()
+    sync()
+    frob.profile_enable(False)
+    return {k: (v[0] / steps, v[1] / steps, v[2] / steps) for k, v in frob.profile_report().items()}
+
+
+def _roofline(prof, clocks):
+    """The dominant kernel (most device time per step) and its algorithmic
+    rate against the FP64 pipe: the derived peak, the measured DFMA rate and
+    the derived peak at the SM clock sampled during the timed region."""
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    launches, ms, fl = prof[top]
+    tot = sum(v[1] for v in prof.values())
+    roof = {"bound": "alu", "kernel": top, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": None, "traffic": None,
+            "peak_source": "FP64 DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts; "
+                           "no FP64 tensor-core kind exists for tcgen05)",
+            "timing": "CUDA events around each launch on its stream, separate profiled pass",
+            "launches_per_step": launches, "ms_per_step": ms, "share_of_step": ms / tot if tot else None,
+            "flops_per_step": fl}
+    if fl > 0 and ms > 0:
+        ach = fl / (ms * 1e-3) / 1e12
+        roof["achieved"] = ach
+        roof["frac"] = ach / FP64_PEAK_TFLOPS
+        roof["frac_vs_measured_dfma"] = ach / FP64_DFMA_MEASURED_TFLOPS
+        mhz = clocks.get("sm_mhz") if clocks else None
+        if mhz:
+            roof["peak_at_sampled_clock"] = 152 * 4 * mhz * 1e6 / 1e12
+            roof["frac_at_sampled_clock"] = ach / roof["peak_at_sampled_clock"]
+    return roof
+
+
+def _kernels(prof):
+    tot = sum(v[1] for v in prof.values()) or 1e-30
+    return {k: {"launches_per_step": v[0], "ms_per_step": round(v[1], 4), "share": round(v[1] / tot, 4),
+                "tflops": (v[2] / (v[1] * 1e-3) / 1e12) if v[2] > 0 and v[1] > 0 else None}
+            for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+
+def _c3_errors(dm, x):
+    """Relative forward error (max norm over Re and Im) against the closed form
+    (I - iB)/(1 - s^2) computed from the rounded B, and ||MX - I||_F /
+    (||M||_F ||X||_F) estimated from every 97th column, both in FP64 on the
+    device."""
+    import numpy as np
+    import torch
+    n = dm.shape[-1]
+    s2 = 1.0 - S_ROT ** 2
+    m64, x64 = dm.to(torch.complex128), x.to(torch.complex128)
+    eye = torch.eye(n, dtype=torch.float64, device=dm.device)
+    exact = torch.complex(eye, -m64.imag) / s2
+    d = x64 - exact
+    fe = (torch.maximum(d.real.abs().max(), d.imag.abs().max()) /
+          torch.maximum(exact.real.abs().max(), exact.imag.abs().max())).item()
+    del d, exact
+    cols = torch.arange(0, n, 97, device=dm.device)
+    r = m64 @ x64[:, cols]
+    r[cols, torch.arange(len(cols), device=dm.device)] -= 1
+    est = r.abs().pow(2).sum().sqrt() * np.sqrt(n / len(cols))
+    res = (est / (torch.linalg.norm(m64) * torch.linalg.norm(x64))).item()
+    return fe, res
 
 
 def residual_fro(m, x):
@@ -147,47 +249,143 @@ def residual_fro(m, x):
     return float(np.linalg.norm(r) / (np.linalg.norm(m) * np.linalg.norm(x)))
 
 
-def cpu_baseline(ms, budget_s=12.0):
-    """Oracle (plain C FP64 Frobenius-Cholesky) on a bounded sample."""
-    import oracle
-    oracle.build()
-    oracle.frob_inv_chol(ms[0])
-    done, t0 = 0, time.perf_counter()
-    while done < len(ms) and time.perf_counter() - t0 < budget_s:
-        oracle.frob_inv_chol(ms[done])
-        done += 1
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "inversions/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} of the {len(ms)} n={N_ORDER} HPD matrices, oracle frob_inv_chol (plain C FP64, "
-                      f"OpenMP), {dt:.1f} s"}
-
-
-def measure_batched(frob, dev, steps, rank):
-    """1024 matrices with n uniform in [32, 512], A, B iid N(0, 1): the mixed
-    Frobenius form and the FP64 complex-LU baseline, both through
-    frob_inv_batched (one call per step, a fixed launch sequence), timed as
-    CUDA-graph replays of the call (and eagerly, for reference)."""
+def measure_config1(frob, dev, reps=20):
+    """n = 256, A, B iid N(0, 1) (seed 1): microseconds per inversion of one
+    matrix, Frobenius vs complex LU, residual and forward error against
+    numpy's LAPACK inverse."""
     import numpy as np
     import torch
     from paper_2208_01239_gb300 import workloads as W
-    sizes, mats = W.uneven_batch(1024, 32, 512, seed=4 + 1000 * rank)
-    out = {"workload": "uneven_1024_n32-512_c128", "sum_n3": float(np.sum(np.asarray(sizes, dtype=np.float64) ** 3))}
-    for name, op, prec in (("frob_inv mixed_bf16", "frob_inv", "mixed_bf16"), ("cplx_lu_inv fp64", "cplx_lu_inv", "fp64")):
-        plan = frob.Batched(sizes, op=op, prec=prec, device=dev)
-        for dst, m in zip(plan.inputs, mats):
-            dst.copy_(torch.from_numpy(m))
+    n = 256
+    m = W.gaussian(n, 1, seed=1)[0]
+    dm = torch.from_numpy(m).to(dev)
+    ref = np.linalg.inv(m)
+    out = {"workload": "gaussian_n256_c128", "n": n, "kappa": float(np.linalg.cond(m))}
+    for name in ("frob_inv", "cplx_lu_inv"):
+        f = getattr(frob, name)
+        ws = torch.empty(frob.workspace_bytes(name, n, 1) + 256, dtype=torch.uint8, device=dev)
+        x = torch.empty_like(dm)
+        info = torch.zeros((1, 32), dtype=torch.uint8, device=dev)
+        step = lambda: f(dm, out=x, ws=ws, info=info, check=False)
+        for _ in range(3):
+            step()
+        ms = _timed(step, reps, torch.cuda.current_stream(dev), lambda: torch.cuda.synchronize(dev)) / reps
+        xn = x.cpu().numpy()
+        out[name] = {"us_per_inversion": 1e3 * ms, "inversions_per_s": 1e3 / ms,
+                     "residual_fro": residual_fro(m, xn),
+                     "forward_error_vs_lapack": float(np.abs(xn - ref).max() / np.abs(ref).max())}
+    return out
+
+
+def measure_config2(frob, dev, steps, warmup, world):
+    """64 x n = 512 HPD, M = Q diag(lam) Q^H, lam log-uniform on [1, 1e4]
+    (seed 2): Frobenius-Cholesky vs complex Cholesky in FP64, and the mixed
+    precision (FP32 start, refinement with FP64-accurate products on the
+    BF16 tensor cores) of both: the Frobenius start and the complex-Cholesky
+    start (the control), at ns_tol 1e-14 and 1e-15; forward error against the
+    closed form Q diag(1/lam) Q^H on three matrices."""
+    import numpy as np
+    import torch
+    from paper_2208_01239_gb300 import workloads as W
+    n, batch = 512, 64
+    ms, qs, lams = W.hpd(n, batch=batch, seed=2, return_parts=True)
+    dm = torch.from_numpy(ms).to(dev)
+    x = torch.empty_like(dm)
+    info = torch.zeros((batch, 32), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sync = lambda: torch.cuda.synchronize(dev)
+    sample = (0, batch // 2, batch - 1)
+    exact = {b: W.hpd_exact_inverse(qs[b], lams[b]) for b in sample}
+    out = {"workload": "hpd_batch64_n512_c128", "n": n, "batch": batch, "lam": "log-uniform [1, 1e4]"}
+    cases = [("frob_inv_hpd fp64", frob.frob_inv_hpd, "fp64", None),
+             ("cplx_chol_inv fp64", frob.cplx_chol_inv, "fp64", None),
+             ("frob_inv_hpd mixed_bf16 tol1e-14", frob.frob_inv_hpd, "mixed_bf16", 1e-14),
+             ("cplx_chol_inv mixed_bf16 tol1e-14 (control)", frob.cplx_chol_inv, "mixed_bf16", 1e-14),
+             ("frob_inv_hpd mixed_bf16 tol1e-15", frob.frob_inv_hpd, "mixed_bf16", 1e-15),
+             ("cplx_chol_inv mixed_bf16 tol1e-15 (control)", frob.cplx_chol_inv, "mixed_bf16", 1e-15)]
+    for name, f, prec, tol in cases:
+        op = "frob_inv_hpd" if f is frob.frob_inv_hpd else "cplx_chol_inv"
+        ws = torch.empty(frob.workspace_bytes(op, n, batch, prec) + 256, dtype=torch.uint8, device=dev)
+        kw = {} if tol is None else {"ns_tol": tol}
+        step = lambda: f(dm, prec=prec, out=x, ws=ws, info=info, check=False, **kw)
+        for _ in range(warmup):
+            step()
+        t = _timed(step, steps, stream, sync) / steps
+        inf = frob.parse_info(info)
+        xn = x.cpu().numpy()
+        row = {"ms_per_step": t, "inversions_per_s": world * batch / (t * 1e-3),
+               "status_ok": int((inf["status"] == 0).sum()),
+               "residual_fro_max_sampled": max(residual_fro(ms[b], xn[b]) for b in sample),
+               "forward_error_max_sampled": max(float(np.abs(xn[b] - exact[b]).max() / np.abs(exact[b]).max())
+                                                for b in sample)}
+        if prec != "fp64":
+            row["ns_iters_hist"] = np.bincount(inf["ns_iters"], minlength=1).tolist()
+            prof = _profile(frob, step, 1, sync)
+            row["top_kernels_ms"] = {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:5]}
+        out[name] = row
+        del ws
+    fp = out["frob_inv_hpd fp64"]["inversions_per_s"]
+    out["speedups"] = {
+        "fp64: frob_inv_hpd / cplx_chol_inv": fp / out["cplx_chol_inv fp64"]["inversions_per_s"],
+        "mixed 1e-14 frob / fp64 cplx_chol": out["frob_inv_hpd mixed_bf16 tol1e-14"]["inversions_per_s"] /
+        out["cplx_chol_inv fp64"]["inversions_per_s"],
+        "mixed 1e-14 frob / mixed 1e-14 complex control": out["frob_inv_hpd mixed_bf16 tol1e-14"]["inversions_per_s"] /
+        out["cplx_chol_inv mixed_bf16 tol1e-14 (control)"]["inversions_per_s"],
+        "mixed 1e-15 frob / mixed 1e-15 complex control": out["frob_inv_hpd mixed_bf16 tol1e-15"]["inversions_per_s"] /
+        out["cplx_chol_inv mixed_bf16 tol1e-15 (control)"]["inversions_per_s"]}
+    return out
+
+
+def measure_config3_fp32_n8192(frob, dev, m_host_c128, steps):
+    """The headline construction at n = 8192 in FP32 (complex64 in and out):
+    Frobenius vs complex LU, time per inversion and the sampled residual.
+    (FP32 cannot resolve S = (1 - s^2) I here; the forward errors at n = 512
+    are in ill_conditioned_fp32.)"""
+    import torch
+    n = m_host_c128.shape[-1]
+    dm = m_host_c128.to(dev).to(torch.complex64)
+    x = torch.empty_like(dm)
+    info = torch.zeros((1, 32), dtype=torch.uint8, device=dev)
+    sync = lambda: torch.cuda.synchronize(dev)
+    out = {"workload": "ill_conditioned_n8192_c64", "n": n}
+    for name in ("frob_inv", "cplx_lu_inv"):
+        f = getattr(frob, name)
+        ws = torch.empty(frob.workspace_bytes(name, n, 1, "fp32") + 256, dtype=torch.uint8, device=dev)
+        step = lambda: f(dm, prec="fp32", out=x, ws=ws, info=info, check=False)
+        step()
+        t = _timed(step, steps, torch.cuda.current_stream(dev), sync) / steps
+        _, res = _c3_errors(dm, x)
+        out[name] = {"ms_per_inversion": t, "inversions_per_s": 1e3 / t, "residual_fro_sampled": res}
+        del ws
+    return out
+
+
+def measure_batched(frob, dev, steps, world, rank):
+    """1024 matrices with n uniform in [32, 512], A, B iid N(0, 1) (seed 4),
+    partitioned across ranks by shard.partition (longest processing time on
+    n^3); per rank one frob_inv_batched call per step, timed as CUDA-graph
+    replays of the call, the slowest rank setting the time.  Forms: mixed
+    Frobenius (FP32 start + BF16-tensor-core refinement), its control (an
+    FP32 complex-LU start with the same refinement) and FP64 complex LU."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2208_01239_gb300 import shard
+    from paper_2208_01239_gb300 import workloads as W
+    sizes, mats = W.uneven_batch(1024, 32, 512, seed=4)
+    mine = shard.partition(sizes, world)[rank]
+    my_sizes = [int(sizes[i]) for i in mine]
+    out = {"workload": "uneven_1024_n32-512_c128", "sum_n3": float(np.sum(np.asarray(sizes, dtype=np.float64) ** 3)),
+           "sharding": f"shard.partition over {world} rank(s); rank 0 holds {len(mine)} matrices"}
+    cases = (("frob_inv mixed_bf16", "frob_inv", "mixed_bf16"),
+             ("cplx_lu_inv mixed_bf16 (control)", "cplx_lu_inv", "mixed_bf16"),
+             ("cplx_lu_inv fp64", "cplx_lu_inv", "fp64"))
+    for name, op, prec in cases:
+        plan = frob.Batched(my_sizes, op=op, prec=prec, device=dev)
+        for dst, i in zip(plan.inputs, mine):
+            dst.copy_(torch.from_numpy(mats[i]))
         plan.run()
         torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            plan.run()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms_eager = e0.elapsed_time(e1) / steps
-        # the same call captured once in a CUDA graph and replayed (the fixed
-        # launch sequence of frob_inv_batched is capture-safe)
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
@@ -198,26 +396,91 @@ def measure_batched(frob, dev, steps, rank):
             plan.run()
         graph.replay()
         torch.cuda.synchronize(dev)
-        e0.record()
-        for _ in range(steps):
-            graph.replay()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / steps
+
+        def barrier():
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+
+        ms = _timed(graph.replay, steps, torch.cuda.current_stream(dev), barrier) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
         inf = plan.info()
         worst = 0.0
-        for k in range(0, 1024, 128):
-            m = torch.from_numpy(mats[k]).to(dev)
+        for k in range(0, len(mine), 128):
+            m = torch.from_numpy(mats[mine[k]]).to(dev)
             x = plan.outputs[k]
             r = m @ x - torch.eye(m.shape[0], dtype=m.dtype, device=dev)
             worst = max(worst, (torch.linalg.norm(r) / (torch.linalg.norm(m) * torch.linalg.norm(x))).item())
         out[name] = {"ms_per_step": ms, "inversions_per_s": 1024 / (ms * 1e-3), "timing": "CUDA graph replay",
-                     "ms_per_step_eager": ms_eager, "inversions_per_s_eager": 1024 / (ms_eager * 1e-3),
-                     "status_ok": int((inf["status"] == 0).sum()), "residual_fro_max_sampled": worst}
+                     "status_ok_rank0": int((inf["status"] == 0).sum()), "residual_fro_max_sampled": worst}
+        if prec != "fp64":
+            out[name]["ns_iters_hist"] = np.bincount(inf["ns_iters"], minlength=1).tolist()
         del graph
         del plan
-    a, b = out["frob_inv mixed_bf16"], out["cplx_lu_inv fp64"]
-    out["speedup_vs_cplx_lu"] = b["ms_per_step"] / a["ms_per_step"]
+    a = out["frob_inv mixed_bf16"]["ms_per_step"]
+    out["speedups"] = {"mixed frob vs fp64 cplx_lu": out["cplx_lu_inv fp64"]["ms_per_step"] / a,
+                       "mixed frob vs mixed complex control": out["cplx_lu_inv mixed_bf16 (control)"]["ms_per_step"] / a}
+    return out
+
+
+def measure_config5(frob, dev, reps=2):
+    """Differentiation: 16 complex FP32 matrices of order 1024, A, B iid
+    N(0, 1)/sqrt(n) + 2I (seed 5), W Gaussian (seed 6), 10 Newton sign steps
+    X <- (X + X^{-1})/2, loss Re tr(W^H sign(M)); forward + backward time and
+    peak device memory above the inputs, with the inverse by FrobInv (the
+    library's Frobenius inversion and adjoint) and by torch.linalg.inv,
+    each with and without per-step checkpointing."""
+    import torch
+    import torch.utils.checkpoint as cp
+    from paper_2208_01239_gb300 import autograd as AG
+    from paper_2208_01239_gb300 import workloads as W
+    n, batch, iters = 1024, 16, 10
+    m, w = W.sign_workload(n, batch=batch, seed=5, w_seed=6)
+    dm = torch.from_numpy(m).to(dev)
+    dw = torch.from_numpy(w).to(dev)
+
+    def torch_loss(mm, ckpt):
+        step = lambda x: 0.5 * (x + torch.linalg.inv(x))
+        x = mm
+        for _ in range(iters):
+            x = cp.checkpoint(step, x, use_reentrant=False) if ckpt else step(x)
+        return (dw.conj() * x).real.sum()
+
+    def run(kind, ckpt):
+        mm = dm.clone().requires_grad_(True)
+        loss = AG.sign_loss(mm, dw, iters, checkpoint=ckpt) if kind == "frob" else torch_loss(mm, ckpt)
+        loss.backward()
+        return loss.detach(), mm.grad
+
+    out = {"workload": "sign_newton_b16_n1024_c64", "n": n, "batch": batch, "newton_steps": iters}
+    grads = {}
+    for kind in ("frob", "torch"):
+        for ckpt in (False, True):
+            run(kind, ckpt)
+            torch.cuda.synchronize(dev)
+            torch.cuda.reset_peak_memory_stats(dev)
+            base = torch.cuda.memory_allocated(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                loss, g = run(kind, ckpt)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            peak = torch.cuda.max_memory_allocated(dev) - base
+            grads[(kind, ckpt)] = g
+            out[f"{kind} checkpoint={ckpt}"] = {"ms_fwd_bwd": e0.elapsed_time(e1) / reps,
+                                                "peak_mem_mb": peak / 2 ** 20, "loss": float(loss.item())}
+    gf, gt = grads[("frob", True)], grads[("torch", False)]
+    out["grad_max_abs_diff_frob_vs_torch"] = float((gf - gt).abs().max().item())
+    out["grad_max_abs_torch"] = float(gt.abs().max().item())
+    out["note"] = ("every eigenvalue of this M has positive real part, so sign(M) = I and the gradient vanishes "
+                   "(both routes give ~0); the GPU tests check non-trivial gradients on a shifted workload")
+    out["speedup_fwd_bwd_frob_vs_torch"] = (out["torch checkpoint=False"]["ms_fwd_bwd"] /
+                                            out["frob checkpoint=False"]["ms_fwd_bwd"])
     return out
 
 
@@ -324,6 +587,14 @@ def measure_accuracy(frob, dev):
                         ("aug_real_solve", frob.aug_real_solve)):
             x = f(dm, rhs, check=False).x.cpu().numpy()
             row[name] = {"forward_error": float(np.abs(x - xt).max() / np.abs(xt).max())}
+        # conditioning of the draw: Frobenius inversion works with A and
+        # S = A + B A^{-1} B, complex LU with M; the gap between the two
+        # routes' left residuals set against kappa(S) / kappa(M)
+        a, b = m.real, m.imag
+        sm = a + b @ np.linalg.solve(a, b)
+        km, ka, ks = (float(np.linalg.cond(t)) for t in (m, a, sm))
+        row["conditioning"] = {"kappa_M": km, "kappa_A": ka, "kappa_S": ks, "kappa_S_over_kappa_M": ks / km,
+                               "res_L_frob_over_cplx_lu": row["frob_inv"]["res_L"] / row["cplx_lu_inv"]["res_L"]}
         out[f"n{n}"] = row
     return out
 
@@ -409,15 +680,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--once", action="store_true",
-                    help="run the workload twice (one warm-up call) and exit: the command profiled by ncu")
-    ap.add_argument("--once-mixed", action="store_true",
-                    help="as --once, for the mixed-precision form")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 1024-matrix uneven workload")
-    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-driver workloads (sign, polar, Sylvester)")
-    ap.add_argument("--no-accuracy", action="store_true", help="skip the kappa = 10 accuracy study")
-    ap.add_argument("--batch", type=int, default=BATCH,
-                    help="matrices per step for --once / --once-mixed (profiling a smaller case)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline workload, its complex-LU baseline and the end-to-end number")
+    ap.add_argument("--once", default=None, choices=["frob_inv", "cplx_lu_inv", "frob_inv_hpd_mixed"],
+                    help="run one inversion of the workload twice and exit: the command profiled by ncu")
+    ap.add_argument("--n", type=int, default=N_ORDER, help="order for --once (profiling a smaller case)")
+    ap.add_argument("--batch", type=int, default=64, help="matrices for --once frob_inv_hpd_mixed")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -431,6 +699,7 @@ def main():
     from paper_2208_01239_gb300 import build as fbuild
     from paper_2208_01239_gb300 import flops
     from paper_2208_01239_gb300 import frob
+    from paper_2208_01239_gb300 import workloads as W
 
     world, rank, local = _dist()
     if world > 1:
@@ -439,201 +708,159 @@ def main():
     dev = torch.device("cuda", local)
     fbuild.build()
     lib = frob.load()
-
-    batch_n = args.batch if (args.once or args.once_mixed) else BATCH
-    ms, qs, lams = _gen_inputs(N_ORDER, batch_n, SEED + rank)
-    m_host = torch.from_numpy(ms).pin_memory()
-    m_dev = m_host.to(dev)
-    x_dev = torch.empty_like(m_dev)
-    x_host = torch.empty_like(m_host).pin_memory()
-    need = frob.workspace_bytes("frob_inv_hpd", N_ORDER, batch_n)
-    ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
-    need_c = frob.workspace_bytes("cplx_chol_inv", N_ORDER, batch_n)
-    ws_c = torch.empty(need_c + 256, dtype=torch.uint8, device=dev)
-    info = torch.zeros((batch_n, 32), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        frob.frob_inv_hpd(m_dev, out=x_dev, ws=ws, info=info, check=False)
+    sync = lambda: torch.cuda.synchronize(dev)
 
     if args.once:
-        step()
-        step()
-        torch.cuda.synchronize(dev)
-        frob.check_info(frob.parse_info(info), "frob_inv_hpd")
-        return 0
-    if args.once_mixed:
-        need_m = frob.workspace_bytes("frob_inv_hpd", N_ORDER, batch_n, "mixed_bf16")
-        ws_m = torch.empty(need_m + 256, dtype=torch.uint8, device=dev)
+        if args.once == "frob_inv_hpd_mixed":
+            ms_ = W.hpd(512, batch=args.batch, seed=2)
+            dm = torch.from_numpy(ms_).to(dev)
+            for _ in range(2):
+                frob.frob_inv_hpd(dm, prec="mixed_bf16", check=False)
+            sync()
+            return 0
+        m, _ = W.ill_conditioned(args.n, seed=SEED)
+        dm = torch.from_numpy(m).to(dev)
+        del m
+        f = getattr(frob, args.once)
         for _ in range(2):
-            frob.frob_inv_hpd(m_dev, prec="mixed_bf16", out=x_dev, ws=ws_m, info=info, check=False)
-        torch.cuda.synchronize(dev)
-        frob.check_info(frob.parse_info(info), "frob_inv_hpd mixed")
+            r = f(dm, check=False)
+        sync()
+        frob.check_info(r.info(), args.once)
+        fe, res = _c3_errors(dm, r.x)
+        print(f"{args.once} n={args.n}: forward error {fe:.3e}, residual {res:.3e}", flush=True)
         return 0
-
-    def step_baseline():
-        frob.cplx_chol_inv(m_dev, out=x_dev, ws=ws_c, info=info, check=False)
 
     def barrier():
         if world > 1:
             dist.barrier()
-        torch.cuda.synchronize(dev)
+        sync()
 
-    def timed(fn, steps):
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        ev0.record(stream)
-        for _ in range(steps):
-            fn()
-        ev1.record(stream)
-        barrier()
-        ms_ = ev0.elapsed_time(ev1)
+    def max_over_ranks(ms_):
         if world > 1:
             t = torch.tensor([ms_], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
+            return float(t.item())
         return ms_
 
-    # warm-up and correctness of the timed configuration
+    n = N_ORDER
+    t_gen = time.perf_counter()
+    m_np, _ = W.ill_conditioned(n, seed=SEED)
+    t_gen = time.perf_counter() - t_gen
+    m_host = torch.from_numpy(m_np).pin_memory()
+    del m_np
+    m_dev = m_host.to(dev)
+    x_dev = torch.empty_like(m_dev)
+    x_host = torch.empty_like(m_host).pin_memory()
+    ws = torch.empty(frob.workspace_bytes("frob_inv", n, 1) + 256, dtype=torch.uint8, device=dev)
+    info = torch.zeros((1, 32), dtype=torch.uint8, device=dev)
+
+    def step():
+        frob.frob_inv(m_dev, out=x_dev, ws=ws, info=info, check=False)
+
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize(dev)
-    inf = frob.parse_info(info)
-    frob.check_info(inf, "frob_inv_hpd")
-    x0 = x_dev.cpu().numpy()
-    res = max(residual_fro(ms[b], x0[b]) for b in (0, BATCH // 2, BATCH - 1))
+    sync()
+    frob.check_info(frob.parse_info(info), "frob_inv")
+    fe, res = _c3_errors(m_dev, x_dev)
 
-    # timed region (device): K steps, clocks sampled meanwhile
+    # timed region: K steps, clocks sampled meanwhile
     launches0 = lib.frob_kernel_launches()
     clk = _clock_sampler()
     time.sleep(0.3)
-    t_ms = timed(step, args.steps)
+    t_ms = max_over_ranks(_timed(step, args.steps, stream, barrier))
     clocks = _clock_summary(clk, local)
     launches = lib.frob_kernel_launches() - launches0
     ms_per_step = t_ms / args.steps
-    value = world * BATCH / (ms_per_step * 1e-3)
-    # per-kernel device times: a separate profiled pass of the same steps, in
-    # which the library brackets every launch with CUDA events on its stream
-    # and runs batch slices one after the other (so each kernel runs alone)
-    prof_steps = min(args.steps, 3)
-    frob.profile_enable(True)
-    tp_ms = timed(step, prof_steps) / prof_steps
-    frob.profile_enable(False)
-    prof = {k: (v[0] * args.steps / prof_steps, v[1] * args.steps / prof_steps)
-            for k, v in frob.profile_report().items()}
+    value = world * 1.0 / (ms_per_step * 1e-3)
+    frob.check_info(frob.parse_info(info), "frob_inv")
 
-    # baseline on the same GPU (complex Cholesky inversion)
-    for _ in range(args.warmup):
-        step_baseline()
-    tb_ms = timed(step_baseline, args.steps) / args.steps
-    torch.cuda.synchronize(dev)
-    xb = x_dev.cpu().numpy()
-    res_b = max(residual_fro(ms[b], xb[b]) for b in (0, BATCH // 2, BATCH - 1))
+    # per-kernel device time and algorithmic flops: a separate profiled step
+    prof = _profile(frob, step, 1, sync)
+    roof = _roofline(prof, clocks)
 
-    # the mixed form on the same workload: FP32 Cholesky-Frobenius start,
-    # Newton-Schulz refinement with FP64-accurate products on the BF16 tensor
-    # cores, same residual gate; at the default tolerance (7-digit residuals)
-    # and at 1e-15 (8-digit residuals, a residual floor near the FP64 paths')
-    need_m = frob.workspace_bytes("frob_inv_hpd", N_ORDER, BATCH, "mixed_bf16")
-    ws_m = torch.empty(need_m + 256, dtype=torch.uint8, device=dev)
+    # the complex-LU inverse on the same GPU and input (fewer steps)
+    kb = max(2, min(args.steps, 5))
+    ws_c = torch.empty(frob.workspace_bytes("cplx_lu_inv", n, 1) + 256, dtype=torch.uint8, device=dev)
+    xb = torch.empty_like(m_dev)
 
-    def measure_mixed(tol):
-        def step_mixed():
-            frob.frob_inv_hpd(m_dev, prec="mixed_bf16", out=x_dev, ws=ws_m, info=info, check=False, ns_tol=tol)
+    def step_b():
+        frob.cplx_lu_inv(m_dev, out=xb, ws=ws_c, info=info, check=False)
 
-        for _ in range(args.warmup):
-            step_mixed()
-        torch.cuda.synchronize(dev)
-        tm_ms = timed(step_mixed, args.steps) / args.steps
-        frob.profile_enable(True)
-        timed(step_mixed, args.steps)
-        frob.profile_enable(False)
-        prof_m = frob.profile_report()
-        inf_m = frob.parse_info(info)
-        xm = x_dev.cpu().numpy()
-        res_m = max(residual_fro(ms[b], xm[b]) for b in (0, BATCH // 2, BATCH - 1))
-        tot_m = max(sum(v[1] for v in prof_m.values()), 1e-30)
-        return {"name": "frob_inv_hpd prec=mixed_bf16", "ns_tol": tol, "value": world * BATCH / (tm_ms * 1e-3),
-                "unit": "inversions/s", "ms_per_step": tm_ms, "residual_fro_max_sampled": res_m,
-                "residual_fro_max_device": float(inf_m["residual"].max()),
-                "status_ok": int((inf_m["status"] == 0).sum()),
-                "ns_iters_hist": np.bincount(inf_m["ns_iters"], minlength=1).tolist(),
-                "dtype": "bf16 tensor cores + fp32 (results FP64-accurate)",
-                "top_kernels": {k: round(v[1] / args.steps, 3) for k, v in
-                                sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]},
-                "top_share": {k: round(v[1] / tot_m, 3) for k, v in
-                              sorted(prof_m.items(), key=lambda kv: -kv[1][1])[:6]}}
+    step_b()
+    sync()
+    frob.check_info(frob.parse_info(info), "cplx_lu_inv")
+    fe_b, res_b = _c3_errors(m_dev, xb)
+    tb_ms = max_over_ranks(_timed(step_b, kb, stream, barrier)) / kb
+    prof_b = _profile(frob, step_b, 1, sync)
+    del ws_c, xb
 
-    mixed = measure_mixed(1e-14)
-    mixed_fine = measure_mixed(1e-15)
+    # end to end through the public API with host buffers: the input copied
+    # in from pinned host memory and the inverse copied out, every step
+    ke = max(2, min(args.steps, 5))
 
-    batched = None if args.no_batched else measure_batched(frob, dev, max(2, min(args.steps, 3)), rank)
-    solve = None if args.no_batched else measure_solve(frob, dev, 3)
-    newton = None if (args.no_newton or args.no_batched) else measure_newton(frob, dev)
-    accuracy = None if (args.no_accuracy or args.no_batched) else measure_accuracy(frob, dev)
-    config3_fp32 = None if (args.no_accuracy or args.no_batched) else measure_config3_fp32(frob, dev)
-
-    # end to end through the public API with host buffers
     def e2e_step():
         m_dev.copy_(m_host, non_blocking=True)
-        frob.frob_inv_hpd(m_dev, out=x_dev, ws=ws, info=info, check=False)
+        frob.frob_inv(m_dev, out=x_dev, ws=ws, info=info, check=False)
         x_host.copy_(x_dev, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
-    te_ms = timed(e2e_step, args.steps) / args.steps
-    bytes_io = BATCH * N_ORDER * N_ORDER * 16
+    e2e_step()
+    te_ms = max_over_ranks(_timed(e2e_step, ke, stream, barrier)) / ke
+    bytes_io = n * n * 16
+    del ws
 
-    # the dominant kernel family by device time, and its algorithmic rate
-    alg = algorithmic_flops(N_ORDER, BATCH)
-    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-            "traffic": None, "kernel": top,
-            "peak_source": "FP64 DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; measured 1.19)",
-            "timing": "CUDA events around each launch on its stream, profiled pass with batch slices serialised",
-            "profiled_ms_per_step": tp_ms}
-    if top in alg:
-        launches_top, ms_top = prof[top]
-        ach = alg[top] * args.steps / (ms_top * 1e-3) / 1e12
-        roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS, launches_per_step=launches_top / args.steps,
-                    flops_per_step=alg[top], ms_per_launch=ms_top / launches_top,
-                    traffic=TRAFFIC_PER_LAUNCH.get(top))
-
-    exec_flops = flops.executed("frob_chol", N_ORDER) * BATCH
-    tflops_exec = exec_flops / (ms_per_step * 1e-3) / 1e12
-    tflops_nom = flops.nominal(N_ORDER) * BATCH / (ms_per_step * 1e-3) / 1e12
-
+    exec_f = flops.executed("frob_lu", n)
+    exec_b = flops.executed("cplx_lu", n)
+    nominal = flops.nominal(n)
     line = {
         "metric": METRIC, "value": value, "unit": "inversions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_ORDER, "batch": BATCH, "seed": SEED,
-                   "lam": "log-uniform [1, 1e4]", "l2": "inputs (268 MB) larger than L2, no flush"},
-        "tflops_executed": tflops_exec, "tflops_nominal_8n3": tflops_nom,
-        "residual_fro_max_sampled": res,
-        "baseline_gpu": {"name": "cplx_chol_inv", "value": world * BATCH / (tb_ms * 1e-3), "unit": "inversions/s",
-                         "ms_per_step": tb_ms, "residual_fro_max_sampled": res_b,
-                         "tflops_executed": flops.executed("cplx_chol", N_ORDER) * BATCH / (tb_ms * 1e-3) / 1e12},
+        "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "s": S_ROT,
+                   "construction": "A = I, B = Q blockdiag([[0,-s],[s,0]]) Q^T, Q Haar orthogonal (Sec. 3)",
+                   "l2": "input (1.07 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "tflops_executed": exec_f / (ms_per_step * 1e-3) / 1e12,
+        "tflops_nominal_8n3": nominal / (ms_per_step * 1e-3) / 1e12,
+        "forward_error_vs_closed_form": fe, "residual_fro_sampled": res,
+        "baseline_gpu": {"name": "cplx_lu_inv fp64", "value": world / (tb_ms * 1e-3), "unit": "inversions/s",
+                         "ms_per_step": tb_ms, "steps": kb, "tflops_executed": exec_b / (tb_ms * 1e-3) / 1e12,
+                         "tflops_nominal_8n3": nominal / (tb_ms * 1e-3) / 1e12,
+                         "forward_error_vs_closed_form": fe_b, "residual_fro_sampled": res_b,
+                         "top_kernels": dict(list(_kernels(prof_b).items())[:5])},
+        "speedup_vs_cplx_lu": tb_ms / ms_per_step,
+        "flops_note": "executed 26 n^3/3 (Frobenius) vs 8 n^3 (complex LU, identity right-hand side exploited); "
+                      "the paper's counts are 28 n^3/3 vs 32 n^3/3 (Sec. 4.1)",
         "roofline": roof,
-        "path_roofline": {"bound": "alu", "achieved": tflops_exec, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                          "frac": tflops_exec / FP64_PEAK_TFLOPS, "what": "whole step, executed FP64 flops"},
-        "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
-                        "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)} for k, v in prof.items()},
-        "mixed": mixed,
-        "mixed_tol_1e-15": mixed_fine,
-        "batched_uneven": batched,
-        "linear_solve": solve,
-        "newton_drivers": newton,
-        "accuracy_kappa10": accuracy,
-        "ill_conditioned_fp32": config3_fp32,
-        "e2e": {"value": world * BATCH / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
-                "d2h_bytes_per_step": bytes_io},
+        "path_roofline": {"bound": "alu", "achieved": exec_f / (ms_per_step * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": exec_f / (ms_per_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                          "what": "whole step, executed FP64 flops"},
+        "kernels": _kernels(prof),
+        "e2e": {"value": world / (te_ms * 1e-3), "unit": "inversions/s", "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io, "steps": ke},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "input_generation_s": t_gen,
     }
+    del x_dev, m_dev
+    torch.cuda.empty_cache()
+
+    if not args.no_extras:
+        line["config1_gaussian_n256"] = measure_config1(frob, dev)
+        line["config2_hpd_b64_n512"] = measure_config2(frob, dev, args.steps, args.warmup, world)
+        line["config3_fp32_n8192"] = measure_config3_fp32_n8192(frob, dev, m_host, 2)
+        line["config4_batched_uneven"] = measure_batched(frob, dev, max(2, min(args.steps, 3)), world, rank)
+        line["config5_autograd"] = measure_config5(frob, dev)
+        line["linear_solve"] = measure_solve(frob, dev, 3)
+        line["newton_drivers"] = measure_newton(frob, dev)
+        line["accuracy_kappa10"] = measure_accuracy(frob, dev)
+        line["ill_conditioned_fp32"] = measure_config3_fp32(frob, dev)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(ms)
+        sec, runs, cores = _cpu_sample(12.0)
+        line["cpu_baseline"] = {
+            "value": _cpu_rate(sec), "unit": "inversions/s", "cores": cores, "kind": "oracle",
+            "sample": f"{runs} oracle frob_inv_lu runs (plain C FP64, OpenMP) of the same construction at "
+                      f"n={CPU_SAMPLE_ORDER}, {sec:.3f} s each, rate scaled to n={n} by n^3"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -61,8 +61,12 @@ typedef enum {
 typedef enum {
   FROB_FP64 = 0,       /* complex128 in and out, FP64 arithmetic throughout */
   FROB_FP32 = 1,       /* complex64 in and out, FP32 arithmetic throughout */
-  FROB_MIXED_TF32 = 2, /* complex128 in and out; TF32 tensor cores + refinement */
-  FROB_MIXED_BF16 = 3  /* complex128 in and out; BF16 tensor cores + refinement */
+  FROB_MIXED_TF32 = 2, /* reserved: every entry point returns FROB_ERR_UNSUPPORTED
+                          (a TF32 start does not contract at the workloads'
+                          condition numbers; no separate TF32 path exists) */
+  FROB_MIXED_BF16 = 3  /* complex128 in and out; FP32 start on the CUDA cores,
+                          refinement with FP64-accurate products on the BF16
+                          tensor cores */
 } frob_prec;
 
 /* Operation codes for frob_workspace_bytes(). */
@@ -130,7 +134,7 @@ size_t frob_workspace_bytes(int op, int n, int batch, int prec);
  *   M, ldm, sm input base, leading dimension (>= n), batch stride (elements)
  *   X, ldx, sx output base, leading dimension, batch stride (elements)
  *   opts       NULL or options.  FROB_FP64 / FROB_FP32: the algorithm in that
- *              precision.  FROB_MIXED_BF16 / FROB_MIXED_TF32 (n <= 512,
+ *              precision.  FROB_MIXED_BF16 (n <= 512,
  *              complex128 in and out): X0 by the FP32 algorithm, then
  *              Newton-Schulz refinement X <- X + X (I - M X) until
  *              ||I - M X||_F/(||M||_F ||X||_F) <= opts->ns_tol, at most
@@ -162,7 +166,9 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
  * cplx_lu_inv -- the baseline: inversion in complex arithmetic by LU with
  * partial pivoting (Sec. 4, Algorithm "Inversion with LU decomposition"):
  * M = P^T L U, then M^{-1} = U^{-1} L^{-1} P.  Arguments as for frob_inv;
- * `prec` is FROB_FP64 (complex128) or FROB_FP32 (complex64).
+ * `prec` is FROB_FP64 (complex128) or FROB_FP32 (complex64), or
+ * FROB_MIXED_BF16: cplx_inv_mixed(FROB_OP_CPLX_LU, ...) with the default
+ * refinement options.
  */
 frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
                         int prec, void* ws, size_t wsb, frob_info* info, void* stream);
@@ -171,9 +177,28 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
  * cplx_chol_inv -- the HPD baseline: inversion in complex arithmetic by
  * Cholesky (Sec. 4.3, Algorithm "Inversion with Cholesky decomposition"):
  * M = R^H R, R^H X1 = I, R X2 = X1, M^{-1} = X2.  Lower triangle read.
+ * `prec` as for cplx_lu_inv (FROB_MIXED_BF16: the refined control).
  */
 frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
                           int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream);
+
+/*
+ * cplx_inv_mixed -- the control for the mixed-precision Frobenius forms (no
+ * counterpart in the paper, which has no mixed precision): X0 by complex LU
+ * (op = FROB_OP_CPLX_LU) or complex Cholesky (op = FROB_OP_CPLX_CHOL, lower
+ * triangle read) inversion in FP32, then exactly the Newton-Schulz
+ * refinement of frob_inv's FROB_MIXED_BF16 mode (the same digit-split
+ * residual and correction products, tolerance and iteration limit from
+ * opts).  Comparing it with frob_inv / frob_inv_hpd at FROB_MIXED_BF16
+ * separates what Frobenius inversion contributes from what the refinement
+ * does.  opts: NULL (FROB_MIXED_BF16, ns_tol 1e-14, ns_max_iter 8) or with
+ * prec = FROB_MIXED_BF16, almost_sure = 0, part = FROB_PART_A.  n <= 512;
+ * complex128 in and out; workspace frob_workspace_bytes(op, n, batch,
+ * FROB_MIXED_BF16).  Other arguments and results as for frob_inv's mixed
+ * mode.
+ */
+frob_status cplx_inv_mixed(int op, int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
+                           int64_t sx, const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream);
 
 /*
  * frob_inv_hpd_noalloc -- frob_inv_hpd in FP64 for callers that cannot
@@ -374,7 +399,11 @@ uint64_t frob_kernel_launches(void);
  * kernel launch of the library with a pair of CUDA events recorded on the
  * launching stream; frob_profile_enable(0) stops recording.
  * frob_profile_report() waits for the recorded events, writes a JSON object
- * {"<kernel variant>": [launches, total_ms], ...} into buf (truncated to len
+ * {"<kernel variant>": [launches, total_ms, flops], ...} into buf (flops: the
+ * real floating-point operations the launches were asked to compute, 2 M N K
+ * per real product and 8 M N K per complex one over the tiles a product
+ * computes, plus the substitutions of the triangular solves; 0 for kernels
+ * that do not count them) (truncated to len
  * bytes, NUL-terminated), releases the records and returns the length needed
  * including the NUL.  Not for use inside CUDA graph capture.  While profiling
  * is on, a call whose batch is split over internal streams runs the slices

@@ -34,12 +34,16 @@ static int debug_level() {
 struct ProfRec {
   const char* name;
   cudaEvent_t a, b;
+  double flops;
 };
 static std::mutex g_prof_mu;
 static std::atomic<int> g_prof_on{0};
 static std::vector<ProfRec> g_prof_recs;
 static std::vector<cudaEvent_t> g_prof_pool;
-static thread_local ProfRec t_pending{nullptr, nullptr, nullptr};
+static thread_local ProfRec t_pending{nullptr, nullptr, nullptr, 0.0};
+static thread_local double t_next_flops = 0.0;
+
+void set_launch_flops(double flops) { t_next_flops = flops; }
 
 static cudaEvent_t prof_event() {
   if (!g_prof_pool.empty()) {
@@ -58,9 +62,11 @@ void launch_begin(const char* name, cudaStream_t st) {
     std::fprintf(stderr, "[frob] launch %s\n", name);
     std::fflush(stderr);
   }
+  const double flops = t_next_flops;
+  t_next_flops = 0.0;
   if (g_prof_on.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    t_pending = ProfRec{name, prof_event(), prof_event()};
+    t_pending = ProfRec{name, prof_event(), prof_event(), flops};
     cudaEventRecord(t_pending.a, st);
   }
 }
@@ -69,7 +75,7 @@ void launch_end(const char* name, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEventRecord(t_pending.b, st);
     g_prof_recs.push_back(t_pending);
-    t_pending = ProfRec{nullptr, nullptr, nullptr};
+    t_pending = ProfRec{nullptr, nullptr, nullptr, 0.0};
   }
   if (debug_level()) {
     cudaError_t e1 = cudaGetLastError();
@@ -92,7 +98,9 @@ frob_opts default_opts() {
 }
 
 bool valid_prec(int p) { return p == FROB_FP64 || p == FROB_FP32; }
-bool mixed_prec(int p) { return p == FROB_MIXED_TF32 || p == FROB_MIXED_BF16; }
+// FROB_MIXED_TF32 has no path of its own (its start would need TF32 operands,
+// which do not contract at the workloads' condition numbers): unsupported.
+bool mixed_prec(int p) { return p == FROB_MIXED_BF16; }
 
 size_t elem_bytes(int prec) { return prec == FROB_FP32 ? 8 : 16; }
 
@@ -278,7 +286,7 @@ extern "C" {
 size_t frob_workspace_bytes(int op, int n, int batch, int prec) {
   if (n < 1 || batch < 1) return 0;
   if (mixed_prec(prec))
-    return ((op == FROB_OP_INV || op == FROB_OP_INV_HPD) && n <= 512)
+    return (op >= FROB_OP_INV && op <= FROB_OP_CPLX_CHOL && n <= 512)
                ? split_ws(batch, [&](int b) { return mixed::mixed_ws(n, b); })
                : 0;
   if (!valid_prec(prec)) return 0;
@@ -386,9 +394,36 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
   return launched();
 }
 
+frob_status cplx_inv_mixed(int op, int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
+                           int64_t sx, const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
+  if (op != FROB_OP_CPLX_LU && op != FROB_OP_CPLX_CHOL) return FROB_ERR_ARG;
+  frob_opts o = opts ? *opts : default_opts();
+  if (!opts) o.prec = FROB_MIXED_BF16;
+  if (o.almost_sure || o.part != FROB_PART_A || o.reserved != 0) return FROB_ERR_ARG;
+  frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb, frob_workspace_bytes(op, n, batch, o.prec),
+                               info, o.prec);
+  if (s != FROB_OK) return s;
+  if (!mixed_prec(o.prec) || n > 512) return FROB_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  frob_status ms = FROB_OK;
+  const TuneKey key{op, o.prec, n, batch};
+  split_run(batch, ws, st, [&](int b) { return mixed::mixed_ws(n, b); },
+            [&](int first, int count, void* w, cudaStream_t s2) {
+              frob_status r = mixed::mixed_run(n, count, in_view<zd>(M, ldm, sm).at_batch(first),
+                                               out_view<zd>(X, ldx, sx).at_batch(first), o, w, info + first, s2,
+                                               op == FROB_OP_CPLX_CHOL, true);
+              if (r != FROB_OK) ms = r;
+            }, &key, wsb);
+  return ms != FROB_OK ? ms : launched();
+}
+
 frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx, int64_t sx,
                         int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
-  if (mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
+  if (mixed_prec(prec)) {
+    frob_opts o = default_opts();
+    o.prec = prec;
+    return cplx_inv_mixed(FROB_OP_CPLX_LU, n, batch, M, ldm, sm, X, ldx, sx, &o, ws, wsb, info, stream);
+  }
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_CPLX_LU, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
@@ -409,7 +444,11 @@ frob_status cplx_lu_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm
 
 frob_status cplx_chol_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, void* X, int64_t ldx,
                           int64_t sx, int prec, void* ws, size_t wsb, frob_info* info, void* stream) {
-  if (mixed_prec(prec)) return FROB_ERR_UNSUPPORTED;
+  if (mixed_prec(prec)) {
+    frob_opts o = default_opts();
+    o.prec = prec;
+    return cplx_inv_mixed(FROB_OP_CPLX_CHOL, n, batch, M, ldm, sm, X, ldx, sx, &o, ws, wsb, info, stream);
+  }
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_CPLX_CHOL, n, batch, prec), info, prec);
   if (s != FROB_OK) return s;
@@ -581,13 +620,18 @@ void frob_profile_enable(int on) {
 
 size_t frob_profile_report(char* buf, size_t len) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  std::map<std::string, std::pair<long, double>> acc;
+  struct Acc {
+    long launches = 0;
+    double ms = 0.0, flops = 0.0;
+  };
+  std::map<std::string, Acc> acc;
   for (auto& r : g_prof_recs) {
     float ms = 0.f;
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       auto& e = acc[r.name];
-      e.first += 1;
-      e.second += ms;
+      e.launches += 1;
+      e.ms += ms;
+      e.flops += r.flops;
     }
     g_prof_pool.push_back(r.a);
     g_prof_pool.push_back(r.b);
@@ -596,8 +640,8 @@ size_t frob_profile_report(char* buf, size_t len) {
   std::string out = "{";
   bool first = true;
   for (auto& kv : acc) {
-    char tmp[96];
-    std::snprintf(tmp, sizeof(tmp), "[%ld, %.6f]", kv.second.first, kv.second.second);
+    char tmp[128];
+    std::snprintf(tmp, sizeof(tmp), "[%ld, %.6f, %.6e]", kv.second.launches, kv.second.ms, kv.second.flops);
     out += (first ? "\"" : ", \"") + kv.first + "\": " + tmp;
     first = false;
   }

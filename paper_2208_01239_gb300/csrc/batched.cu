@@ -213,10 +213,14 @@ extern "C" frob_status frob_inv_batched(int op, int batch, const int32_t* n_host
         s = frob_inv_hpd(N, cnt, L.pin, N, NN, L.pout, N, NN, &o, L.sws, L.sws_bytes, L.tinfo, stream);
         break;
       case FROB_OP_CPLX_LU:
-        s = cplx_lu_inv(N, cnt, L.pin, N, NN, L.pout, N, NN, o.prec, L.sws, L.sws_bytes, L.tinfo, stream);
+        s = o.prec == FROB_MIXED_BF16
+                ? cplx_inv_mixed(op, N, cnt, L.pin, N, NN, L.pout, N, NN, &o, L.sws, L.sws_bytes, L.tinfo, stream)
+                : cplx_lu_inv(N, cnt, L.pin, N, NN, L.pout, N, NN, o.prec, L.sws, L.sws_bytes, L.tinfo, stream);
         break;
       default:
-        s = cplx_chol_inv(N, cnt, L.pin, N, NN, L.pout, N, NN, o.prec, L.sws, L.sws_bytes, L.tinfo, stream);
+        s = o.prec == FROB_MIXED_BF16
+                ? cplx_inv_mixed(op, N, cnt, L.pin, N, NN, L.pout, N, NN, &o, L.sws, L.sws_bytes, L.tinfo, stream)
+                : cplx_chol_inv(N, cnt, L.pin, N, NN, L.pout, N, NN, o.prec, L.sws, L.sws_bytes, L.tinfo, stream);
         break;
     }
     if (s != FROB_OK) return s;

@@ -164,6 +164,10 @@ enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
 // time can be read back with frob_profile_report.
 void launch_begin(const char* name, cudaStream_t st);
 void launch_end(const char* name, cudaStream_t st);
+// The algorithmic flops of the next launch of this host thread (2 M N K for
+// a product, over the tiles it computes), kept in its profile record and
+// summed per kernel variant by frob_profile_report; 0 when not set.
+void set_launch_flops(double flops);
 // cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) once per
 // (kernel, device, bytes): the attribute belongs to the function on the
 // current device, so a process that drives several GPUs sets it on each.

@@ -1289,11 +1289,11 @@ __global__ void __launch_bounds__(SLU_THREADS, 1) getrf_small_kernel(int n, MatB
 //   1. every CTA finds its local candidate (largest key, lowest row) and
 //      publishes it with a copy of that row; CTA 0 also publishes row j;
 //   2. a grid barrier (bounded wait);
-//   3. every CTA reduces the G candidates in the same order (the same pivot
-//      as the one-CTA kernels: largest key, ties to the lowest row, NaN
-//      never wins), the owner of row j takes the pivot row, the owner of the
-//      pivot row takes the old row j, and every CTA scales and updates its
-//      rows below j with the pivot row.
+//   3. every CTA fetches all candidates and their rows in one round trip to
+//      L2, reduces the keys in the same order (the same pivot as the one-CTA
+//      kernels: largest key, ties to the lowest row, NaN never wins), the
+//      owner of row j takes the pivot row, the owner of the pivot row takes
+//      the old row j, and every CTA scales and updates its rows below j.
 // The candidates are double-buffered by the parity of j, so one barrier per
 // column suffices: a CTA can only overwrite buffer j mod 2 after every CTA
 // has passed the barrier of column j + 1, i.e. has finished reading it.
@@ -1303,7 +1303,7 @@ __global__ void __launch_bounds__(SLU_THREADS, 1) getrf_small_kernel(int n, MatB
 // FROB_ERR_TIMEOUT and skips every later wait of the call; the results are
 // then unusable but no CTA hangs.
 constexpr int MC_THREADS = 256;
-constexpr int MC_GMAX = 256;         // cooperating CTAs per matrix, at most
+constexpr int MC_GMAX = 64;          // cooperating CTAs per matrix, at most
 constexpr int MC_MIN_ROWS = 128;     // rows per CTA, at least
 constexpr int MC_BATCH_MAX = 16;     // matrices per call that take this path
 constexpr size_t MC_SMEM_MAX = 200 * 1024;
@@ -1328,6 +1328,11 @@ template <typename T> constexpr size_t mc_jrow_off() {
 template <typename T> constexpr size_t mc_scratch_per_matrix() {
   return mc_jrow_off<T>() + ((2 * PANEL_MAX * sizeof(T) + 255) & ~(size_t)255);
 }
+// dynamic shared memory of a CTA holding R panel rows: the rows (stride
+// PANEL_MAX + 1), then the G candidate rows and the old row j
+template <typename T> constexpr size_t mc_smem(int R) {
+  return sizeof(T) * ((size_t)R * (PANEL_MAX + 1) + (size_t)(MC_GMAX + 1) * PANEL_MAX);
+}
 
 // loads through L2 (not L1, which is not coherent across SMs) of values
 // another CTA wrote
@@ -1347,9 +1352,17 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 
-// Barrier of the G CTAs of one matrix (sense by generation count).  Returns
-// true when this or an earlier wait of the call gave up.
+// Barrier of the G CTAs of one matrix (sense by generation count).  The
+// CTA's writes before it are ordered by the CTA barrier and published by the
+// releasing arrival (release is cumulative); the acquiring load that sees
+// the new generation orders every read after the closing CTA barrier.
+// Returns true when this or an earlier wait of the call gave up.
 __device__ __forceinline__ bool mc_barrier(McHdr* h, unsigned G, long long limit_cycles) {
   __shared__ int s_gaveup;
   __syncthreads();
@@ -1357,12 +1370,10 @@ __device__ __forceinline__ bool mc_barrier(McHdr* h, unsigned G, long long limit
     int gaveup = *reinterpret_cast<volatile int*>(&h->err);
     if (!gaveup) {
       const unsigned g = ld_acquire_u32(&h->gen);
-      __threadfence();
-      const unsigned arrived = atomicAdd(&h->count, 1u) + 1u;
+      const unsigned arrived = atom_add_release_u32(&h->count, 1u) + 1u;
       if (arrived == G) {
-        atomicExch(&h->count, 0u);
-        __threadfence();
-        atomicAdd(&h->gen, 1u);
+        atomicExch(&h->count, 0u);  // every CTA has arrived; none re-arrives before the new generation
+        atom_add_release_u32(&h->gen, 1u);
       } else {
         const long long t0 = clock64();
         while (ld_acquire_u32(&h->gen) == g) {
@@ -1371,10 +1382,8 @@ __device__ __forceinline__ bool mc_barrier(McHdr* h, unsigned G, long long limit
             gaveup = 1;
             break;
           }
-          __nanosleep(20);
         }
       }
-      __threadfence();
     }
     s_gaveup = gaveup;
   }
@@ -1399,10 +1408,12 @@ __global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k
   T* rows = reinterpret_cast<T*>(s + mc_rows_off<T>());
   T* jrow = reinterpret_cast<T*>(s + mc_jrow_off<T>());
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* P = reinterpret_cast<T*>(smraw);
+  T* P = reinterpret_cast<T*>(smraw);       // [R][PS]
+  T* cand = P + (size_t)R * PS;             // [MC_GMAX][PANEL_MAX]
+  T* jr = cand + (size_t)MC_GMAX * PANEL_MAX;  // [PANEL_MAX]
   __shared__ KeyIdx<K> red[MC_THREADS / 32];
   __shared__ int redbad[MC_THREADS / 32];
-  __shared__ T pr[PANEL_MAX];
+  __shared__ McKey<K> sk[MC_GMAX];
   __shared__ T s_rinv;
   __shared__ int s_lwin, s_win, s_p, s_ok;
   T* g = A.at(b) + (int64_t)(k0 + row0) * A.ld + k0;
@@ -1456,15 +1467,28 @@ __global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k
       if (c == 0 && t == 0) report(info, b, FROB_ERR_TIMEOUT, info_off + k0 + j + 1);
       break;
     }
-    // 3. the pivot, the same in every CTA (candidates reduced in CTA order);
-    // its row was published by the CTA that owns it, p / R
+    // 3. every candidate, its row and the old row j, fetched at once
+    for (int e = t; e < G * kb; e += MC_THREADS)
+      cand[(e / kb) * PANEL_MAX + (e % kb)] = ldcg_(&rows[((int64_t)par * MC_GMAX + e / kb) * PANEL_MAX + (e % kb)]);
+    if (t < G) {
+      const McKey<K>* kp = keys + par * MC_GMAX + t;
+      McKey<K> kk;
+      kk.key = __ldcg(&kp->key);
+      kk.idx = __ldcg(&kp->idx);
+      kk.bad = __ldcg(&kp->bad);
+      sk[t] = kk;
+    }
+    if (t >= MC_THREADS - PANEL_MAX && t - (MC_THREADS - PANEL_MAX) < kb)
+      jr[t - (MC_THREADS - PANEL_MAX)] = ldcg_(&jrow[par * PANEL_MAX + t - (MC_THREADS - PANEL_MAX)]);
+    __syncthreads();
+    // the pivot, the same in every CTA (candidates reduced in CTA order); its
+    // row is the candidate of the CTA that owns it, p / R
     if (t < 32) {
       KeyIdx<K> bb{(K)-1, 0x7fffffff};
       int anybad = 0;
       for (int q = t; q < G; q += 32) {
-        const McKey<K>* kp = keys + par * MC_GMAX + q;
-        anybad |= __ldcg(&kp->bad);
-        bb = kmax(bb, KeyIdx<K>{__ldcg(&kp->key), __ldcg(&kp->idx)});
+        anybad |= sk[q].bad;
+        bb = kmax(bb, KeyIdx<K>{sk[q].key, sk[q].idx});
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -1474,25 +1498,26 @@ __global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k
       anybad = __any_sync(0xffffffffu, anybad);
       if (t == 0) {
         const bool none = bb.idx == 0x7fffffff;
-        s_p = none ? j : bb.idx;
-        s_win = none ? -1 : bb.idx / R;
-        s_ok = !anybad && bb.key > (K)0;
+        const int p = none ? j : bb.idx;
+        const int win = none ? -1 : bb.idx / R;
+        const bool ok = !anybad && bb.key > (K)0;
+        s_p = p;
+        s_win = win;
+        s_ok = ok;
+        s_rinv = ok ? recip_(cand[win * PANEL_MAX + j]) : one_v<T>();
+        if (c == 0) {
+          piv[(int64_t)b * n + k0 + j] = k0 + p;
+          if (!ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+        }
       }
     }
     __syncthreads();
     const int p = s_p;
-    if (t < kb) pr[t] = s_win >= 0 ? ldcg_(&rows[((int64_t)par * MC_GMAX + s_win) * PANEL_MAX + t]) : P[j * PS + t];
-    __syncthreads();
+    const T* pr = s_win >= 0 ? cand + s_win * PANEL_MAX : P + j * PS;  // the pivot row
     if (p != j && t < kb) {
-      if (c == 0) P[j * PS + t] = pr[t];
-      if (p >= row0 && p < row0 + rc) P[(p - row0) * PS + t] = ldcg_(&jrow[par * PANEL_MAX + t]);
-    }
-    if (t == 0) {
-      if (c == 0) {
-        piv[(int64_t)b * n + k0 + j] = k0 + p;
-        if (!s_ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
-      }
-      s_rinv = s_ok ? recip_(pr[j]) : one_v<T>();
+      const T pv = pr[t];
+      if (p >= row0 && p < row0 + rc) P[(p - row0) * PS + t] = jr[t];
+      if (c == 0) P[j * PS + t] = pv;
     }
     __syncthreads();
     // scale column j below the pivot, then the rank-1 update of the rest
@@ -1502,15 +1527,19 @@ __global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k
         if (row0 + lr > j) P[lr * PS + j] = mul_(P[lr * PS + j], rinv);
     }
     __syncthreads();
-    const int w = kb - j - 1;
-    if (w > 0)
-      for (int e = t; e < rc * w; e += MC_THREADS) {
-        const int lr = e / w, cc = j + 1 + e % w;
-        if (row0 + lr > j) mac(P[lr * PS + cc], neg_(P[lr * PS + j]), pr[cc]);
+    // rows by thread modulo MC_THREADS / 2, the columns j + 1 + h, j + 3 + h, ...
+    // by half h of the CTA
+    {
+      constexpr int HALF = MC_THREADS / 2;
+      const int h = t / HALF;
+      for (int lr = t % HALF; lr < rc; lr += HALF) {
+        if (row0 + lr <= j) continue;
+        const T l = neg_(P[lr * PS + j]);
+        for (int cc = j + 1 + h; cc < kb; cc += 2) mac(P[lr * PS + cc], l, pr[cc]);
       }
+    }
     __syncthreads();
   }
-  __syncthreads();
   for (int e = t; e < rc * kb; e += MC_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[(e / kb) * PS + (e % kb)];
 }
 

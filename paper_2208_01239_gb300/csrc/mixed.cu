@@ -1,6 +1,8 @@
 // Mixed-precision Frobenius inversion with Newton-Schulz refinement.
 //
-//   X_0      = Frobenius inversion of M in FP32 (Sec. 4.1, on the CUDA cores)
+//   X_0      = Frobenius inversion of M in FP32 (Sec. 4.1, on the CUDA cores);
+//              for the control runs, complex LU / Cholesky inversion in FP32
+//              instead (the refinement below is the same for both starts)
 //   repeat:  R = I - M X        FP64-accurate (digit-split products on the
 //                               BF16 tensor cores, ozaki.cuh)
 //            stop when ||R||_F / (||M||_F ||X||_F) <= tol
@@ -11,6 +13,7 @@
 // rows).  Matrices that have converged, or whose FP32 inversion failed, are
 // skipped by every later kernel through a per-matrix flag, so the loop needs
 // no host synchronisation and a fixed launch sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -285,9 +288,11 @@ Layout carve(int n, int batch, void* ws) {
   const int Kp = (n + oz::KP_ALIGN - 1) / oz::KP_ALIGN * oz::KP_ALIGN;
   L.M32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
   L.X32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
-  const size_t w_lu = frob_lu_ws<float>(n, batch, nullptr, nullptr);
-  const size_t w_ch = frob_chol_ws<float>(n, batch, nullptr, nullptr);
-  L.ws32 = take(w_lu > w_ch ? w_lu : w_ch);
+  size_t w32 = frob_lu_ws<float>(n, batch, nullptr, nullptr);
+  w32 = std::max(w32, frob_chol_ws<float>(n, batch, nullptr, nullptr));
+  w32 = std::max(w32, cplx_lu_ws<zf>(n, batch, nullptr, nullptr));
+  w32 = std::max(w32, cplx_chol_ws<zf>(n, batch, nullptr, nullptr));
+  L.ws32 = take(w32);
   L.Mp = static_cast<double*>(take(2 * nn * batch * 8));
   L.Xp = static_cast<double*>(take(2 * nn * batch * 8));
   L.XTp = static_cast<double*>(take(2 * nn * batch * 8));
@@ -313,7 +318,7 @@ Layout carve(int n, int batch, void* ws) {
 size_t mixed_ws(int n, int batch) { return carve(n, batch, nullptr).bytes; }
 
 frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
-                      cudaStream_t st, bool hpd) {
+                      cudaStream_t st, bool hpd, bool complex_start) {
   if (n > oz::K_MAX) return FROB_ERR_UNSUPPORTED;
   Layout L = carve(n, batch, ws);
   const int Kp = (n + oz::KP_ALIGN - 1) / oz::KP_ALIGN * oz::KP_ALIGN;
@@ -327,13 +332,20 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   FROB_LAUNCH("mixed_conv_in", st,
               conv_in_kernel<<<eg, 256, 0, st>>>(n, M, MatB<zf>{L.M32, n, nn}, L.Mp, L.nM2, hpd ? 1 : 0));
   // X_0: Frobenius inversion in FP32, with LU (Sec. 4.1) or, for Hermitian
-  // positive definite input, with Cholesky (Sec. 4.3); also initialises info
+  // positive definite input, with Cholesky (Sec. 4.3); or, for the control,
+  // complex LU / Cholesky inversion in FP32; also initialises info
   frob_opts o32 = o;
   o32.prec = FROB_FP32;
-  if (hpd)
-    frob_chol_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, L.ws32, info, st);
+  const MatB<const zf> M32{L.M32, n, nn};
+  const MatB<zf> X32{L.X32, n, nn};
+  if (complex_start && hpd)
+    cplx_chol_run<zf>(n, batch, M32, X32, L.ws32, info, st);
+  else if (complex_start)
+    cplx_lu_run<zf>(n, batch, M32, X32, L.ws32, info, st);
+  else if (hpd)
+    frob_chol_run<float>(n, batch, M32, X32, L.ws32, info, st);
   else
-    frob_lu_run<float>(n, batch, MatB<const zf>{L.M32, n, nn}, MatB<zf>{L.X32, n, nn}, o32, L.ws32, info, st);
+    frob_lu_run<float>(n, batch, M32, X32, o32, L.ws32, info, st);
   FROB_LAUNCH("mixed_conv_x", st, conv_x_kernel<<<eg, 256, 0, st>>>(n, MatB<const zf>{L.X32, n, nn}, L.Xp, L.XTp, batch));
   FROB_LAUNCH("mixed_init_skip", st, init_skip_kernel<<<(batch + 127) / 128, 128, 0, st>>>(info, L.skip, batch));
   const int s_resid = tol < 1e-14 ? S_RESID_FINE : S_RESID;

@@ -239,7 +239,7 @@ bool overlaps(const void* a, int64_t lda, int64_t sa, int ra, int ca, const void
 }
 bool valid_prec_for(int route, int prec) {
   if (prec == FROB_FP64 || prec == FROB_FP32) return true;
-  return route == FROB_ROUTE_FROB && (prec == FROB_MIXED_BF16 || prec == FROB_MIXED_TF32);
+  return route == FROB_ROUTE_FROB && prec == FROB_MIXED_BF16;
 }
 
 frob_opts opts_of(const frob_opts* opts) {

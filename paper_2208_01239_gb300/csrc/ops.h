@@ -65,10 +65,12 @@ void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB
                  MatB<typename cplx_of<R>::type> out, void* ws, cudaStream_t st);
 
 namespace mixed {
-// Mixed-precision Frobenius inversion with Newton-Schulz refinement (n <= 512).
+// Mixed-precision Frobenius inversion with Newton-Schulz refinement (n <= 512);
+// complex_start: the FP32 start is complex LU / Cholesky inversion instead
+// (the control that separates the refinement's gain from Frobenius's).
 size_t mixed_ws(int n, int batch);
 frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob_opts& o, void* ws, frob_info* info,
-                      cudaStream_t st, bool hpd);
+                      cudaStream_t st, bool hpd, bool complex_start = false);
 }  // namespace mixed
 
 }  // namespace frob

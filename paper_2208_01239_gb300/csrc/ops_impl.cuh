@@ -152,10 +152,30 @@ constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
 
 template <typename T> inline int panel_width() { return PANEL_MAX; }
 
+// real flops of one multiply-add of T
+template <typename T> constexpr double madd_flops() { return is_cplx<T>::value ? 8.0 : 2.0; }
+
+// The multiply-adds gemm_kernel computes for (M, N, K, tile_mode): its K
+// range per 64 x 64 tile (see the tile modes), clipped to the matrix.
+inline double gemm_madds(int M, int N, int K, int tile_mode) {
+  if (tile_mode == 0) return (double)M * N * K;
+  double total = 0.0;
+  for (int i0 = 0; i0 < M; i0 += TB)
+    for (int j0 = 0; j0 < N; j0 += TB) {
+      if ((tile_mode & 1) && j0 > i0 + TB - 1) continue;
+      int kbeg = (tile_mode & 2) ? std::max(i0, j0) : 0;
+      if ((tile_mode & 4) && j0 > kbeg) kbeg = j0;
+      const int kend = ((tile_mode & 8) && i0 + TB < K) ? i0 + TB : K;
+      if (kend > kbeg) total += (double)std::min(TB, M - i0) * std::min(TB, N - j0) * (kend - kbeg);
+    }
+  return total;
+}
+
 template <typename T, int OPA, int OPB, class Epi>
 inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<const T> B, Epi epi, int tile_mode,
                         cudaStream_t st, int npairs = 1, int shift = 0) {
   if (M <= 0 || N <= 0) return;
+  set_launch_flops(madd_flops<T>() * gemm_madds(M, N, K, tile_mode) * batch * npairs);
   dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch * npairs);
   static const std::string name = std::string("gemm<") + type_tag<T>() + ",op" + std::to_string(OPA) + ",op" +
                                   std::to_string(OPB) + "," + Epi::tag + ">";
@@ -188,6 +208,12 @@ inline void trsm(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T> Bm,
   dim3 grid((nrhs + TB - 1) / TB, 1, batch);
   for (int s = 0; s < nblk; ++s) {
     int kb = LOWER ? s : nblk - 1 - s;
+    {
+      // the product over the finished block rows and the substitution
+      const int r0 = kb * TB, rows = std::min(TB, n - r0);
+      const int kfin = LOWER ? r0 : n - r0 - rows;
+      set_launch_flops(madd_flops<T>() * ((double)rows * nrhs * kfin + 0.5 * rows * rows * nrhs) * batch);
+    }
     static const std::string name = std::string("trsm<") + type_tag<T>() + ",op" + std::to_string(OPT) +
                                     (LOWER ? ",lower" : ",upper") + (UNIT ? ",unit" : "") + (RHS_I ? ",rhs=I" : "") +
                                     ">";
@@ -362,10 +388,10 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
     if (mc && m > PANEL_THREADS) {
       R = std::max(MC_MIN_ROWS, (m + gcap - 1) / gcap);
       G = (m + R - 1) / R;
-      if ((size_t)R * (PANEL_MAX + 1) * sizeof(T) > MC_SMEM_MAX) G = 0;
+      if (mc_smem<T>(R) > MC_SMEM_MAX) G = 0;
     }
     if (G > 0) {
-      const size_t smem = (size_t)R * (PANEL_MAX + 1) * sizeof(T);
+      const size_t smem = mc_smem<T>(R);
       int64_t bs = (int64_t)mc_scratch_per_matrix<T>();
       long long limit = 1ll << 31;  // about a second of SM clock
       void* args[] = {(void*)&n, (void*)&k0, (void*)&kb, (void*)&A, (void*)&piv, (void*)&info, (void*)&info_off,

@@ -96,6 +96,8 @@ def load() -> ctypes.CDLL:
             f = getattr(lib, name)
             f.argtypes = common + [i32, vp, sz, vp, vp]
             f.restype = i32
+        lib.cplx_inv_mixed.argtypes = [i32] + common + [ctypes.POINTER(FrobOpts), vp, sz, vp, vp]
+        lib.cplx_inv_mixed.restype = i32
         lib.frob_status_str.argtypes = [i32]
         lib.frob_status_str.restype = ctypes.c_char_p
         lib.frob_version.argtypes = []
@@ -180,14 +182,16 @@ def profile_enable(on: bool = True):
 
 
 def profile_report() -> dict:
-    """{kernel variant: (launches, total device ms)} since profile_enable."""
+    """{kernel variant: (launches, total device ms, algorithmic flops)} since
+    profile_enable (flops 0 for kernels that do not count them)."""
     import json
     lib = load()
     buf = ctypes.create_string_buffer(1 << 20)
     need = int(lib.frob_profile_report(buf, len(buf)))
     if need > len(buf):
         raise RuntimeError("profile report truncated")
-    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+    return {k: (int(v[0]), float(v[1]), float(v[2]) if len(v) > 2 else 0.0)
+            for k, v in json.loads(buf.value.decode()).items()}
 
 
 def status_str(code: int) -> str:
@@ -261,6 +265,8 @@ def _call(op: str, m: torch.Tensor, prec: str, opts: FrobOpts | None, out: torch
         if op in ("frob_inv", "frob_inv_hpd"):
             st = getattr(lib, op)(*args, ctypes.byref(opts) if opts is not None else None, ws_ptr, ws_bytes,
                                   info.data_ptr(), stream)
+        elif opts is not None:  # the complex inverses' refined control (cplx_inv_mixed)
+            st = lib.cplx_inv_mixed(OP[op], *args, ctypes.byref(opts), ws_ptr, ws_bytes, info.data_ptr(), stream)
         else:
             st = getattr(lib, op)(*args, PREC[prec], ws_ptr, ws_bytes, info.data_ptr(), stream)
     if st != FROB_OK:
@@ -307,14 +313,21 @@ def frob_inv_hpd(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=No
     return _call("frob_inv_hpd", m, prec, _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter), out, ws, info, check)
 
 
-def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
-    """Complex LU inversion with partial pivoting (baseline)."""
-    return _call("cplx_lu_inv", m, prec, None, out, ws, info, check)
+def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True,
+                ns_tol: float = 1e-14, ns_max_iter: int = 8) -> Result:
+    """Complex LU inversion with partial pivoting (baseline).  prec
+    "mixed_bf16": the control for the mixed Frobenius form, an FP32 complex-LU
+    start with the same Newton-Schulz refinement (cplx_inv_mixed)."""
+    opts = _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter) if prec.startswith("mixed") else None
+    return _call("cplx_lu_inv", m, prec, opts, out, ws, info, check)
 
 
-def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True) -> Result:
-    """Complex Cholesky inversion (HPD baseline, lower triangle read)."""
-    return _call("cplx_chol_inv", m, prec, None, out, ws, info, check)
+def cplx_chol_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True,
+                  ns_tol: float = 1e-14, ns_max_iter: int = 8) -> Result:
+    """Complex Cholesky inversion (HPD baseline, lower triangle read); prec
+    "mixed_bf16" as for cplx_lu_inv."""
+    opts = _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter) if prec.startswith("mixed") else None
+    return _call("cplx_chol_inv", m, prec, opts, out, ws, info, check)
 
 
 class Batched:

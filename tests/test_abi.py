@@ -177,6 +177,8 @@ def test_batched_plan_sizes(lib):
     assert ws([32 * k for k in range(1, 66)]) == 0                        # 65 distinct buckets
     assert ws([32 * k for k in range(1, 65)]) > 0                         # 64 are allowed
     assert ws([600], prec=3) == 0 and ws([500], prec=3) > 0               # mixed: n <= 512
+    assert ws([500], op=2, prec=3) > 0 and ws([500], op=3, prec=3) > 0    # the complex refined controls
+    assert ws([500], prec=2) == 0                                         # FROB_MIXED_TF32: unsupported
     assert ws([10], op=7) == 0
 
 

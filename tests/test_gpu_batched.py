@@ -40,8 +40,7 @@ def _check(ms, xs, prec, info, hpd=False):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed_bf16"])
 @pytest.mark.parametrize("op", ["frob_inv", "cplx_lu_inv"])
 def test_batched_uneven_vs_oracle(F, op, prec):
-    if op == "cplx_lu_inv" and prec.startswith("mixed"):
-        pytest.skip("the baselines have no mixed mode")
+    # cplx_lu_inv with mixed_bf16 is the refined control (FP32 complex-LU start)
     dt = np.complex64 if prec == "fp32" else np.complex128
     ms = [W.gaussian(n, 1, seed=900 + i, dtype=dt)[0] for i, n in enumerate(SIZES)]
     xs, info = F.frob_inv_batched([torch.from_numpy(m).cuda() for m in ms], op=op, prec=prec)

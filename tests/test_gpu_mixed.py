@@ -28,12 +28,24 @@ def F():
     return frob
 
 
-@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_tf32"])
+def test_mixed_tf32_is_unsupported(F):
+    """FROB_MIXED_TF32 has no path of its own: every entry point refuses it."""
+    m = torch.from_numpy(W.gaussian(16, 1, seed=1)).cuda()
+    for f in (F.frob_inv, F.frob_inv_hpd, F.cplx_lu_inv, F.cplx_chol_inv):
+        with pytest.raises(F.FrobError) as e:
+            f(m, prec="mixed_tf32")
+        assert e.value.status == F.FROB_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("route", ["frob_inv", "cplx_lu_inv"])
 @pytest.mark.parametrize("n", [1, 7, 33, 64, 100, 128, 200, 256, 512])
-def test_mixed_vs_oracle(F, prec, n):
+def test_mixed_vs_oracle(F, route, n):
+    """The mixed Frobenius form and its control (an FP32 complex-LU start with
+    the same refinement) against the oracle, at the FP64 targets."""
+    prec = "mixed_bf16"
     batch = 3 if n <= 256 else 2
     ms = W.gaussian(n, batch=batch, seed=7000 + n)
-    r = F.frob_inv(torch.from_numpy(ms).cuda(), prec=prec)
+    r = getattr(F, route)(torch.from_numpy(ms).cuda(), prec=prec)
     x = r.x.cpu().numpy()
     info = r.info()
     for b in range(batch):
@@ -66,15 +78,17 @@ def test_mixed_hpd_workload_kappa_1e4(F):
         assert metrics.forward_error(x[b], exact) <= 32 * 256 * kappa * U64
 
 
+@pytest.mark.parametrize("route", ["frob_inv_hpd", "cplx_chol_inv"])
 @pytest.mark.parametrize("n", [5, 64, 129, 512])
-def test_mixed_hpd_route_vs_oracle(F, n):
-    """frob_inv_hpd in the mixed precisions: FP32 Cholesky-Frobenius start
-    (Sec. 4.3), FP64-accurate refinement; lower triangle read."""
+def test_mixed_hpd_route_vs_oracle(F, route, n):
+    """frob_inv_hpd in the mixed precision: FP32 Cholesky-Frobenius start
+    (Sec. 4.3), FP64-accurate refinement; and its control, an FP32 complex
+    Cholesky start with the same refinement; lower triangle read."""
     batch = 3 if n < 512 else 8
     ms, qs, lams = W.hpd(n, batch=batch, seed=8000 + n, return_parts=True)
     bad = ms.copy()
     bad[:, np.triu_indices(n, 1)[0], np.triu_indices(n, 1)[1]] = 9.0 + 9.0j  # upper triangle ignored
-    r = F.frob_inv_hpd(torch.from_numpy(bad).cuda(), prec="mixed_bf16")
+    r = getattr(F, route)(torch.from_numpy(bad).cuda(), prec="mixed_bf16")
     x = r.x.cpu().numpy()
     for b in range(batch):
         exact = W.hpd_exact_inverse(qs[b], lams[b])
@@ -86,13 +100,14 @@ def test_mixed_hpd_route_vs_oracle(F, n):
 
 
 @pytest.mark.parametrize("route,n", [("frob_inv", 33), ("frob_inv", 200), ("frob_inv", 512),
-                                     ("frob_inv_hpd", 129), ("frob_inv_hpd", 512)])
+                                     ("frob_inv_hpd", 129), ("frob_inv_hpd", 512), ("cplx_lu_inv", 200),
+                                     ("cplx_chol_inv", 512)])
 def test_mixed_fine_tolerance(F, route, n):
     """A tolerance below 1e-14 selects 8-digit residual products (pairs
     s + t <= 9): the refinement then reaches relative residuals near 1e-16,
     also for the HPD workload whose large diagonal sets the row scales."""
     batch = 2
-    if route == "frob_inv":
+    if route in ("frob_inv", "cplx_lu_inv"):
         ms = W.gaussian(n, batch=batch, seed=9100 + n)
     else:
         ms = W.hpd(n, batch=batch, seed=9200 + n)

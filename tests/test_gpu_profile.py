@@ -1,0 +1,41 @@
+"""The per-kernel profiler's algorithmic flops (the numerator of the
+benchmark's roofline): summed over one call they equal the executed count of
+the algorithm up to the panel factorizations' lower-order work, which the
+panel kernels do not count."""
+import pytest
+import torch
+
+from paper_2208_01239_gb300 import flops
+from paper_2208_01239_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2208_01239_gb300 import build, frob
+    build.build()
+    frob.load()
+    return frob
+
+
+@pytest.mark.parametrize("op,alg,n", [("frob_inv", "frob_lu", 1088), ("cplx_lu_inv", "cplx_lu", 1088),
+                                      ("frob_inv", "frob_lu", 320)])
+def test_profile_flops_match_executed_count(F, op, alg, n):
+    dm = torch.from_numpy(W.gaussian(n, 1, seed=11)).cuda()
+    f = getattr(F, op)
+    f(dm)
+    torch.cuda.synchronize()
+    F.profile_enable(True)
+    f(dm)
+    torch.cuda.synchronize()
+    F.profile_enable(False)
+    rep = F.profile_report()
+    counted = sum(v[2] for v in rep.values())
+    want = flops.executed(alg, n)
+    # uncounted: the panels and the U12 solves beside them (about 2 x 32 n^2
+    # flops each per factorization) and the triangular inverses' 64 x 64
+    # diagonal blocks; counted beyond the leading order: whole 64 x 64 tiles
+    # on the diagonals of the triangular products
+    assert 0.90 * want <= counted <= 1.03 * want, (counted / want, rep)
+    assert all(v[1] > 0 for v in rep.values())

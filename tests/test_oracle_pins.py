@@ -378,16 +378,31 @@ def test_bicomplex_special_cases(oracle_lib):
     assert np.abs(y0).max() <= 1e-13 and np.abs(y1 + np.linalg.inv(a)).max() <= 1e-12 * np.abs(np.linalg.inv(a)).max()
 
 
-def test_bench_flop_table_sums_to_the_executed_count():
-    """The benchmark's per-kernel algorithmic flops (the numerator of the
-    roofline's achieved rate) add up to the executed count of the
-    Frobenius-Cholesky step, 19 n^3 / 3 per matrix."""
+def test_executed_flop_counts():
+    """The executed counts the benchmark reports: Frobenius inversion with LU
+    26 n^3 / 3 (LU 2/3, two solves 2, product 2, LU 2/3, S^{-1} 4/3, product 2),
+    complex LU inversion 8 n^3 (4 x (2/3 + 4/3)), Frobenius-Cholesky 19 n^3 / 3;
+    and the paper's 28/3 and 32/3 (Sec. 4.1)."""
+    from fractions import Fraction
+    assert flops.EXECUTED["frob_lu"] == Fraction(26, 3)
+    assert flops.EXECUTED["cplx_lu"] == 8
+    assert flops.EXECUTED["frob_chol"] == Fraction(19, 3)
+    assert flops.PAPER["frob_lu"] == Fraction(28, 3) and flops.PAPER["cplx_lu"] == Fraction(32, 3)
+
+
+def test_bench_roofline_arithmetic():
+    """The benchmark's roofline picks the kernel variant with the most device
+    time per step and divides its algorithmic flops by that time."""
     import importlib.util
     import os
     spec = importlib.util.spec_from_file_location(
         "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    n, batch = 512, 64
-    total = sum(bench.algorithmic_flops(n, batch).values())
-    assert abs(total - flops.executed("frob_chol", n) * batch) <= 1e-9 * total
+    prof = {"a": (3.0, 10.0, 1.0e10), "b": (1.0, 30.0, 3.3e10), "c": (5.0, 2.0, 0.0)}
+    r = bench._roofline(prof, {"sm_mhz": 1035.0})
+    assert r["kernel"] == "b"
+    assert abs(r["achieved"] - 3.3e10 / 30e-3 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
+    assert abs(r["peak_at_sampled_clock"] - bench.FP64_PEAK_TFLOPS / 2) < 1e-9
+    assert abs(r["share_of_step"] - 30.0 / 42.0) < 1e-12
