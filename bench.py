@@ -682,10 +682,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload, its complex-LU baseline and the end-to-end number")
-    ap.add_argument("--once", default=None, choices=["frob_inv", "cplx_lu_inv", "frob_inv_hpd_mixed"],
+    ap.add_argument("--once", default=None, choices=["frob_inv", "cplx_lu_inv", "frob_inv_hpd", "frob_inv_hpd_mixed"],
                     help="run one inversion of the workload twice and exit: the command profiled by ncu")
     ap.add_argument("--n", type=int, default=N_ORDER, help="order for --once (profiling a smaller case)")
     ap.add_argument("--batch", type=int, default=64, help="matrices for --once frob_inv_hpd_mixed")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision for --once")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -712,23 +713,28 @@ def main():
     sync = lambda: torch.cuda.synchronize(dev)
 
     if args.once:
-        if args.once == "frob_inv_hpd_mixed":
+        if args.once in ("frob_inv_hpd", "frob_inv_hpd_mixed"):
+            # the 64 x n = 512 HPD workload (seed 2), or its first --batch matrices
             ms_ = W.hpd(512, batch=args.batch, seed=2)
             dm = torch.from_numpy(ms_).to(dev)
+            prec = "mixed_bf16" if args.once == "frob_inv_hpd_mixed" else "fp64"
             for _ in range(2):
-                frob.frob_inv_hpd(dm, prec="mixed_bf16", check=False)
+                r = frob.frob_inv_hpd(dm, prec=prec, check=False)
             sync()
+            frob.check_info(r.info(), args.once)
             return 0
         m, _ = W.ill_conditioned(args.n, seed=SEED)
         dm = torch.from_numpy(m).to(dev)
         del m
+        if args.prec == "fp32":
+            dm = dm.to(torch.complex64)
         f = getattr(frob, args.once)
         for _ in range(2):
-            r = f(dm, check=False)
+            r = f(dm, prec=args.prec, check=False)
         sync()
         frob.check_info(r.info(), args.once)
         fe, res = _c3_errors(dm, r.x)
-        print(f"{args.once} n={args.n}: forward error {fe:.3e}, residual {res:.3e}", flush=True)
+        print(f"{args.once} n={args.n} {args.prec}: forward error {fe:.3e}, residual {res:.3e}", flush=True)
         return 0
 
     def barrier():

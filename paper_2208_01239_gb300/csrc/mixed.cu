@@ -288,8 +288,11 @@ Layout carve(int n, int batch, void* ws) {
   const int Kp = (n + oz::KP_ALIGN - 1) / oz::KP_ALIGN * oz::KP_ALIGN;
   L.M32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
   L.X32 = static_cast<zf*>(take(nn * batch * sizeof(zf)));
-  size_t w32 = frob_lu_ws<float>(n, batch, nullptr, nullptr);
-  w32 = std::max(w32, frob_chol_ws<float>(n, batch, nullptr, nullptr));
+  // the FP32 start runs without tensor-core products (TcOff below): its
+  // workspace ends with their scratch, which is left out
+  const size_t tcb = tc_scratch_for(n, batch);
+  size_t w32 = frob_lu_ws<float>(n, batch, nullptr, nullptr) - tcb;
+  w32 = std::max(w32, frob_chol_ws<float>(n, batch, nullptr, nullptr) - tcb);
   w32 = std::max(w32, cplx_lu_ws<zf>(n, batch, nullptr, nullptr));
   w32 = std::max(w32, cplx_chol_ws<zf>(n, batch, nullptr, nullptr));
   L.ws32 = take(w32);
@@ -338,6 +341,7 @@ frob_status mixed_run(int n, int batch, MatB<const zd> M, MatB<zd> X, const frob
   o32.prec = FROB_FP32;
   const MatB<const zf> M32{L.M32, n, nn};
   const MatB<zf> X32{L.X32, n, nn};
+  TcOff no_tensor_core_start;
   if (complex_start && hpd)
     cplx_chol_run<zf>(n, batch, M32, X32, L.ws32, info, st);
   else if (complex_start)

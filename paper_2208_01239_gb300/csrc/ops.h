@@ -9,6 +9,20 @@
 
 namespace frob {
 
+// Set while the mixed precisions compute their FP32 start: its products stay
+// on the CUDA cores, whose FP32 rounding gives the refinement a closer start
+// than split-TF32 products with tensor-core accumulation (measured: fewer
+// Newton-Schulz steps on the HPD workload).
+inline thread_local bool t_tc_off = false;
+struct TcOff {
+  bool saved;
+  TcOff() : saved(t_tc_off) { t_tc_off = true; }
+  ~TcOff() { t_tc_off = saved; }
+};
+// bytes an FP32 driver reserves for its largest tensor-core product (order n,
+// K = n): the two split operands of tc_gemm.cuh's split-TF32 form
+size_t tc_scratch_for(int n, int batch);
+
 template <typename R> struct cplx_of;
 template <> struct cplx_of<double> { using type = zd; };
 template <> struct cplx_of<float> { using type = zf; };
@@ -20,6 +34,8 @@ template <typename R> struct Planes {
   int* partb;         // [batch] 1: B factored (frob_lu_run)
   frob_info* infoB;   // [batch] status of the LU of B (FROB_PART_AUTO)
   unsigned char* mcs = nullptr;  // scratch of the multi-CTA LU panels (0 bytes when unused)
+  unsigned char* tcs = nullptr;  // scratch of the FP32 tensor-core products (0 bytes when unused)
+  size_t tcs_bytes = 0;
 };
 // Workspace of the complex baselines.
 template <typename C> struct CPlanes {

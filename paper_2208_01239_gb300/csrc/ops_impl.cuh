@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "dense_impl.cuh"
 #include "ops.h"
+#include "tc_gemm.cuh"
 
 namespace frob {
 
@@ -171,11 +172,73 @@ inline double gemm_madds(int M, int N, int K, int tile_mode) {
   return total;
 }
 
+// Tensor-core scratch of the FP32 drivers: while a TcScope is open on this
+// host thread, FP32 products of at least TC3_MIN_MN x TC3_MIN_MN x TC3_MIN_K
+// (full products, no tile skipping) run as split-TF32 tensor-core GEMMs
+// (tc_gemm.cuh) in this scratch instead of on the CUDA cores.  The scratch is
+// the caller's workspace; consecutive products reuse it in stream order.  Its
+// first 256 bytes hold the kernels' timeout flag, reported into the info
+// records when the scope closes.
+struct TcScratch {
+  unsigned char* p = nullptr;
+  size_t bytes = 0;
+  int* err = nullptr;
+};
+inline thread_local TcScratch t_tc;
+
+
+static __global__ void tc_err_report_kernel(const int* err, frob_info* info, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch && *err != 0) report(info, b, FROB_ERR_TIMEOUT, 0);
+}
+
+class TcScope {
+ public:
+  TcScope(unsigned char* p, size_t bytes, frob_info* info, int batch, cudaStream_t st)
+      : saved_(t_tc), info_(info), batch_(batch), st_(st) {
+    if (p && bytes > 256 && !t_tc_off) {
+      t_tc = TcScratch{p, bytes, reinterpret_cast<int*>(p)};
+      cudaMemsetAsync(p, 0, 256, st);
+    } else {
+      t_tc = TcScratch{};
+    }
+  }
+  ~TcScope() {
+    if (t_tc.err && info_)
+      FROB_LAUNCH("tc_err_report", st_,
+                  tc_err_report_kernel<<<(batch_ + 127) / 128, 128, 0, st_>>>(t_tc.err, info_, batch_));
+    t_tc = saved_;
+  }
+  TcScope(const TcScope&) = delete;
+  TcScope& operator=(const TcScope&) = delete;
+
+ private:
+  TcScratch saved_;
+  frob_info* info_;
+  int batch_;
+  cudaStream_t st_;
+};
+
 template <typename T, int OPA, int OPB, class Epi>
 inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<const T> B, Epi epi, int tile_mode,
                         cudaStream_t st, int npairs = 1, int shift = 0) {
   if (M <= 0 || N <= 0) return;
-  set_launch_flops(madd_flops<T>() * gemm_madds(M, N, K, tile_mode) * batch * npairs);
+  const double fl = madd_flops<T>() * gemm_madds(M, N, K, tile_mode) * batch * npairs;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tile_mode == 0 && npairs == 1 && t_tc.p && M >= tc::TC3_MIN_MN && N >= tc::TC3_MIN_MN &&
+        K >= tc::TC3_MIN_K && tc::tc3_scratch_bytes(M, N, K, batch) <= t_tc.bytes) {
+      CUtensorMap ma, mb;
+      // op(A) rows with k contiguous: A as stored (OP_N) or transposed; the B
+      // operand holds op(B)^T, i.e. B transposed (OP_N) or as stored
+      if (tc::tc3_prepare(M, N, K, batch, A.p, A.ld, A.bs, OPA != OP_N, B.p, B.ld, B.bs, OPB == OP_N, t_tc.p, &ma,
+                          &mb, st)) {
+        set_launch_flops(fl);
+        tc::tc3_launch(ma, mb, M, N, K, batch, epi, t_tc.err, st);
+        return;
+      }
+    }
+  }
+  set_launch_flops(fl);
   dim3 grid((N + TB - 1) / TB, (M + TB - 1) / TB, batch * npairs);
   static const std::string name = std::string("gemm<") + type_tag<T>() + ",op" + std::to_string(OPA) + ",op" +
                                   std::to_string(OPB) + "," + Epi::tag + ">";
@@ -497,6 +560,8 @@ size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.partb = c.take<int>((size_t)batch);
   p.infoB = c.take<frob_info>((size_t)batch);
   p.mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n, batch));
+  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0;
+  p.tcs = c.take<unsigned char>(p.tcs_bytes);
   if (out) *out = p;
   return c.off;
 }
@@ -572,6 +637,7 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
                  const frob_opts& o, void* ws, frob_info* info, cudaStream_t st) {
   Planes<R> p;
   frob_lu_ws<R>(n, batch, ws, &p);
+  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st);  // FP32: large products on the tensor cores
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   const bool autop = o.part == FROB_PART_AUTO;
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
@@ -611,6 +677,8 @@ size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.S = plane<R>(c, n, batch);
   p.Bp = plane<R>(c, n, batch);
   p.Y = plane<R>(c, n, batch);
+  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0;
+  p.tcs = c.take<unsigned char>(p.tcs_bytes);
   if (out) *out = p;
   return c.off;
 }
@@ -620,6 +688,7 @@ void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, Ma
                    void* ws, frob_info* info, cudaStream_t st) {
   Planes<R> p;
   frob_chol_ws<R>(n, batch, ws, &p);
+  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st);  // FP32: large products on the tensor cores
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
   potrf<R>(n, batch, p.LA, info, 0, st);                                                 // A = R1^T R1, L1 = R1^T
@@ -960,7 +1029,19 @@ __global__ void adj_out_kernel(int n, MatB<const R> U1, MatB<const R> U2, MatB<c
 template <typename R> size_t adjoint_ws(int n, int batch) {
   Carve c{nullptr};
   for (int k = 0; k < 9; ++k) plane<R>(c, n, batch);
+  c.take<unsigned char>(std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0);
   return c.off;
+}
+
+// the adjoint has no info records: a tensor-core product whose bounded wait
+// gave up turns the whole result into NaN
+template <typename C> __global__ void adj_nan_on_err_kernel(int n, const int* err, MatB<C> out) {
+  if (*err == 0) return;
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  out.at(b)[(int64_t)i * out.ld + j] = C{NAN, NAN};
 }
 
 template <typename R>
@@ -969,6 +1050,9 @@ void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB
   Carve c{static_cast<unsigned char*>(ws)};
   MatB<R> P[9];
   for (int k = 0; k < 9; ++k) P[k] = plane<R>(c, n, batch);
+  const size_t tcb = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0;
+  unsigned char* tcs = c.take<unsigned char>(tcb);
+  TcScope tc_scope(tcs, tcb, nullptr, batch, st);  // FP32: the six products on the tensor cores
   MatB<R>&Xr = P[0], &Xi = P[1], &Xd = P[2], &Gr = P[3], &Gi = P[4], &Gs = P[5], &T1 = P[6], &T2 = P[7], &T3 = P[8];
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   const R one = (R)1, zero = (R)0;
@@ -982,6 +1066,9 @@ void adjoint_run(int n, int batch, MatB<const typename cplx_of<R>::type> X, MatB
   gemm_launch<R, OP_N, OP_T>(n, n, n, batch, cst(T2), cst(Xi), axpby<R>(Gi, one, zero, true), 0, st);
   gemm_launch<R, OP_N, OP_T>(n, n, n, batch, cst(T3), cst(Xd), axpby<R>(Gs, one, zero, true), 0, st);
   FROB_LAUNCH("adj_out", st, adj_out_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, cst(Gr), cst(Gi), cst(Gs), out));
+  if (t_tc.err)
+    FROB_LAUNCH("adj_nan_on_err", st,
+                adj_nan_on_err_kernel<typename cplx_of<R>::type><<<elem_grid(n, batch), 256, 0, st>>>(n, t_tc.err, out));
 }
 
 }  // namespace frob

@@ -12,6 +12,7 @@
 #include "../../include/frobinv.h"
 #include "common.cuh"
 #include "tc_gemm.cuh"
+#include "ops.h"
 
 namespace frob {
 namespace tc {
@@ -86,7 +87,67 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, i
   return cudaGetLastError();
 }
 
+// Split-TF32 operand rows (see tc3_prepare): dst[b][r][blk * Kp + k] for the
+// three blocks, from the element (r, k) of the source, src[r * ld + k] or,
+// with trans, src[k * ld + r]; k in [K, Kp) is written as zero.  32 x 32
+// tiles through shared memory, so both the source and the destination are
+// read / written along their contiguous dimension.  pattern 0 (A operand):
+// hi, hi, lo; pattern 1 (B operand): hi, lo, hi.
+__global__ void __launch_bounds__(256) split3_kernel(int R, int K, int64_t Kp, const float* src, int64_t ld,
+                                                     int64_t sb, int trans, int pattern, float* dst) {
+  __shared__ float tile[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const float* sbp = src + (int64_t)b * sb;
+  for (int i = ty; i < 32; i += 8) {
+    if (trans) {  // tile[k][r] from source row k0 + i, columns r0 + tx
+      const int k = k0 + i, r = r0 + tx;
+      tile[i][tx] = (k < K && r < R) ? sbp[(int64_t)k * ld + r] : 0.f;
+    } else {      // tile[r][k] from source row r0 + i, columns k0 + tx
+      const int r = r0 + i, k = k0 + tx;
+      tile[i][tx] = (k < K && r < R) ? sbp[(int64_t)r * ld + k] : 0.f;
+    }
+  }
+  __syncthreads();
+  float* db = dst + (int64_t)b * R * 3 * Kp;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, k = k0 + tx;
+    if (r >= R || k >= Kp) continue;
+    const float x = trans ? tile[tx][i] : tile[i][tx];
+    const float hi = to_tf32(x);
+    const float lo = to_tf32(x - hi);
+    float* row = db + (int64_t)r * 3 * Kp;
+    row[k] = hi;
+    row[Kp + k] = pattern == 0 ? hi : lo;
+    row[2 * Kp + k] = pattern == 0 ? lo : hi;
+  }
+}
+
 }  // namespace
+
+int64_t tc3_kp(int K) { return ((int64_t)K + 3) / 4 * 4; }
+
+size_t tc3_scratch_bytes(int M, int N, int K, int batch) {
+  const int64_t kp = tc3_kp(K);
+  auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return 256 + a256((size_t)batch * M * 3 * kp * 4) + a256((size_t)batch * N * 3 * kp * 4);
+}
+
+bool tc3_prepare(int M, int N, int K, int batch, const float* A, int64_t lda, int64_t sa, bool transA,
+                 const float* B, int64_t ldb, int64_t sb, bool transB, void* scratch, CUtensorMap* ma,
+                 CUtensorMap* mb, cudaStream_t st) {
+  const int64_t kp = tc3_kp(K);
+  unsigned char* base = static_cast<unsigned char*>(scratch) + 256;
+  float* wa = reinterpret_cast<float*>(base);
+  float* wb = reinterpret_cast<float*>(base + (((size_t)batch * M * 3 * kp * 4 + 255) & ~(size_t)255));
+  const dim3 ga((unsigned)((kp + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)batch);
+  const dim3 gb((unsigned)((kp + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)batch);
+  FROB_LAUNCH("tc_split3", st, split3_kernel<<<ga, 256, 0, st>>>(M, K, kp, A, lda, sa, transA ? 1 : 0, 0, wa));
+  FROB_LAUNCH("tc_split3", st, split3_kernel<<<gb, 256, 0, st>>>(N, K, kp, B, ldb, sb, transB ? 1 : 0, 1, wb));
+  return make_map(ma, wa, 1, (int)(3 * kp), M, batch, 3 * kp, (int64_t)M * 3 * kp, BM) &&
+         make_map(mb, wb, 1, (int)(3 * kp), N, batch, 3 * kp, (int64_t)N * 3 * kp, 256);
+}
 
 int64_t pitch_for(int kind, int K) {
   const int q = kind == 0 ? 8 : 4;  // 16 bytes
@@ -101,6 +162,11 @@ size_t gemm_tc_ws(int kind, int M, int N, int K, int batch) {
 }
 
 }  // namespace tc
+
+size_t tc_scratch_for(int n, int batch) {
+  return n >= tc::TC3_MIN_K ? tc::tc3_scratch_bytes(n, n, n, batch) : 0;
+}
+
 }  // namespace frob
 
 using namespace frob;

@@ -169,6 +169,18 @@ struct TcEpiStoreF32 {
   }
 };
 
+// Adapter for the element-wise epilogues of the CUDA-core GEMM
+// (operator()(b, i, j, v)): the tensor-core kernel hands it 16 columns of one
+// row at a time.
+template <class Epi> struct TcEpiElem {
+  Epi e;
+  __device__ __forceinline__ void operator()(int b, int row, int col0, const float (&v)[16], int nvalid) const {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < nvalid) e(b, row, col0 + i, v[i]);
+  }
+};
+
 // Persistent: CTA c takes output tiles c, c + gridDim.x, ... (x fastest, then
 // y, then the batch).  TMEM holds two BN-column accumulators; the MMA issuer
 // fills one while the epilogue warps drain the other, so a tile's epilogue
@@ -320,6 +332,52 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
+}
+
+// ---------------------------------------------------------------- split TF32
+// FP32 products on the TF32 tensor cores with FP32-level accuracy: every
+// operand value x is split into hi = tf32(x) and lo = tf32(x - hi) (both
+// rounded to nearest; x - hi has at most 13 significant bits, so
+// |x - hi - lo| <= 2^-23 |x|), and a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b
+// (the dropped lo_a lo_b is below 2^-22 |a b|).  The three products are one
+// tensor-core GEMM over a K three times as long: the A operand row holds
+// [hi | hi | lo] and the B operand row [hi | lo | hi], each block of Kp
+// (K padded to a 16-byte multiple with zeros) values, so that the FP32
+// accumulator in TMEM sums all three.
+constexpr int TC3_MIN_MN = 128;  // smaller products stay on the CUDA cores
+constexpr int TC3_MIN_K = 256;   // as do short ones (an epilogue-bound rank-K update)
+
+int64_t tc3_kp(int K);
+// scratch for one product: both split operands (plus the timeout flag's 256 B)
+size_t tc3_scratch_bytes(int M, int N, int K, int batch);
+// Splits op(A) (M x K; A[i][k], or A[k][i] when transA) and op(B)^T (N x K;
+// B[k][j] when transB, else B[j][k]) into the scratch after its first 256
+// bytes and encodes the two tensor maps; false if the maps cannot be made.
+bool tc3_prepare(int M, int N, int K, int batch, const float* A, int64_t lda, int64_t sa, bool transA,
+                 const float* B, int64_t ldb, int64_t sb, bool transB, void* scratch, CUtensorMap* ma,
+                 CUtensorMap* mb, cudaStream_t st);
+
+// One persistent launch of tc_gemm_kernel over the split operands with an
+// element-wise epilogue; `err` receives FROB_ERR_TIMEOUT if a bounded wait
+// gave up.
+template <class Epi>
+inline cudaError_t tc3_launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, int batch, Epi epi,
+                              int* err, cudaStream_t st) {
+  constexpr int BN = 256, STAGES = 4;
+  using S = TcSmem<BN, STAGES>;
+  using E = TcEpiElem<Epi>;
+  set_smem_attr(tc_gemm_kernel<1, BN, STAGES, E>, S::BYTES);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
+  if (tiles > INT32_MAX) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
+  const int K3 = (int)(3 * tc3_kp(K));
+  FROB_LAUNCH("tc_gemm<3xtf32>", st,
+              tc_gemm_kernel<1, BN, STAGES, E><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K3, batch, E{epi},
+                                                                                  err));
+  return cudaGetLastError();
 }
 
 }  // namespace tc

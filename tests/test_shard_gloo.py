@@ -1,7 +1,8 @@
 """Multi-rank host logic on CPU: two gloo ranks shard an uneven batch with
-partition(), each 'inverts' its share (here: records its indices and a cheap
-checksum computed on the host), and the gather covers every matrix exactly
-once with balanced n^3 loads.  No GPU."""
+partition(); the gather covers every matrix exactly once with balanced n^3
+loads, and in a second test each rank inverts its share (through the CPU
+oracle's Frobenius inversion, standing in for the GPU call) and rank 0 checks
+every gathered inverse.  No GPU."""
 import os
 
 import pytest
@@ -54,3 +55,40 @@ def test_two_gloo_ranks_cover_the_batch():
     assert allidx == list(range(1024))
     assert abs(ld[0] - ld[1]) <= 512 ** 3
     assert tmax == 2.0
+
+
+def _invert_worker(rank, world, port, q):
+    import numpy as np
+
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sizes, mats = W.uneven_batch(24, 3, 40, seed=41)
+    parts = shard.partition(sizes, world)
+    nmax = int(max(sizes))
+    # each rank's inverses, zero-padded to nmax x nmax, as (re, im) planes
+    mine = torch.zeros((len(sizes), 2, nmax, nmax), dtype=torch.float64)
+    for i in parts[rank]:
+        x = oracle.frob_inv_lu(mats[i])
+        n = x.shape[0]
+        mine[i, 0, :n, :n] = torch.from_numpy(np.ascontiguousarray(x.real))
+        mine[i, 1, :n, :n] = torch.from_numpy(np.ascontiguousarray(x.imag))
+    dist.all_reduce(mine)  # disjoint shares: the sum is the gather
+    if rank == 0:
+        worst = 0.0
+        for i, n in enumerate(sizes):
+            x = mine[i, 0, :n, :n].numpy() + 1j * mine[i, 1, :n, :n].numpy()
+            r = mats[i] @ x - np.eye(n)
+            worst = max(worst, float(np.linalg.norm(r) / (np.linalg.norm(mats[i]) * np.linalg.norm(x))))
+        q.put(worst)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_invert_their_shares():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 30600 + os.getpid() % 1000
+    mp.start_processes(_invert_worker, args=(2, port, q), nprocs=2, join=True, start_method="spawn")
+    worst = q.get(timeout=60)
+    assert worst <= 1e-13
