@@ -51,6 +51,21 @@ METRIC = "complex inversions/s and TFLOP/s, Frobenius vs complex-LU on 1 GB300, 
 # measured 1.19 TFLOP/s
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 FP64_DFMA_MEASURED_TFLOPS = 1.19
+# BF16 digit products per FP64 product in the tensor-core route of the FP64
+# Frobenius path (eight digits per operand: the pairs s + t <= 9)
+DIGIT_PAIRS = 36
+
+
+def _bf16_peak():
+    """Measured dense BF16 burst of this GPU type (MEASURED_PEAKS.json when
+    present, else the profiling recipe's 1.9 PFLOP/s fallback)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s"
+
+
 # Reference arm and CPU baseline: the oracle's Frobenius inversion with LU on
 # the same construction at this smaller order, scaled to order N_ORDER by n^3
 CPU_SAMPLE_ORDER = 1024
@@ -187,9 +202,17 @@ def _profile(frob, fn, steps, sync):
 
 def _roofline(prof, clocks):
     """The dominant kernel (most device time per step) and its algorithmic
-    rate against the FP64 pipe: the derived peak, the measured DFMA rate and
-    the derived peak at the SM clock sampled during the timed region."""
+    rate against its bound: the FP64 digit-product GEMM against the BF16
+    tensor peak (see _roofline_digits); FP64-pipe kernels against the derived
+    FP64 peak, the measured DFMA rate and the derived peak at the SM clock
+    sampled during the timed region."""
     top = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    if top == "ozr_gemm<f64 digits>":
+        r = _roofline_digits(prof)
+        tot = sum(v[1] for v in prof.values())
+        r["share_of_step"] = prof[top][1] / tot if tot else None
+        r["timing"] = "CUDA events around each launch on its stream, separate profiled pass"
+        return r
     launches, ms, fl = prof[top]
     tot = sum(v[1] for v in prof.values())
     roof = {"bound": "alu", "kernel": top, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -209,6 +232,22 @@ def _roofline(prof, clocks):
             roof["peak_at_sampled_clock"] = 152 * 4 * mhz * 1e6 / 1e12
             roof["frac_at_sampled_clock"] = ach / roof["peak_at_sampled_clock"]
     return roof
+
+
+def _roofline_digits(prof):
+    """The FP64 digit-product GEMM (exact BF16 digit products on the tensor
+    cores): its FP64 flops x DIGIT_PAIRS BF16 products per step against the
+    BF16 peak."""
+    key = "ozr_gemm<f64 digits>"
+    if key not in prof:
+        return None
+    launches, ms, fl = prof[key]
+    peak, src = _bf16_peak()
+    ach = DIGIT_PAIRS * fl / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": key, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src, "launches_per_step": launches, "ms_per_step": ms,
+            "fp64_flops_per_step": fl, "fp64_equivalent_tflops": fl / (ms * 1e-3) / 1e12,
+            "what": f"{DIGIT_PAIRS} BF16 digit products per FP64 multiply-add pair"}
 
 
 def _kernels(prof):
@@ -687,6 +726,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_ORDER, help="order for --once (profiling a smaller case)")
     ap.add_argument("--batch", type=int, default=64, help="matrices for --once frob_inv_hpd_mixed")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision for --once")
+    ap.add_argument("--gemm", default="auto", choices=["auto", "fp64_pipe"],
+                    help="FP64 products for --once frob_inv: digit products on the tensor cores, or the FP64 pipe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -729,8 +770,9 @@ def main():
         if args.prec == "fp32":
             dm = dm.to(torch.complex64)
         f = getattr(frob, args.once)
+        kw = {"gemm": args.gemm} if args.once == "frob_inv" else {}
         for _ in range(2):
-            r = f(dm, prec=args.prec, check=False)
+            r = f(dm, prec=args.prec, check=False, **kw)
         sync()
         frob.check_info(r.info(), args.once)
         fe, res = _c3_errors(dm, r.x)
@@ -785,8 +827,21 @@ def main():
     prof = _profile(frob, step, 1, sync)
     roof = _roofline(prof, clocks)
 
-    # the complex-LU inverse on the same GPU and input (fewer steps)
+    # the same Frobenius inversion with every product on the FP64 pipe (the
+    # like-for-like arithmetic of the complex-LU baseline), fewer steps
     kb = max(2, min(args.steps, 5))
+
+    def step_pipe():
+        frob.frob_inv(m_dev, out=x_dev, ws=ws, info=info, check=False, gemm="fp64_pipe")
+
+    step_pipe()
+    sync()
+    frob.check_info(frob.parse_info(info), "frob_inv fp64_pipe")
+    fe_p, res_p = _c3_errors(m_dev, x_dev)
+    tp_ms = max_over_ranks(_timed(step_pipe, kb, stream, barrier)) / kb
+    prof_p = _profile(frob, step_pipe, 1, sync)
+
+    # the complex-LU inverse on the same GPU and input (fewer steps)
     ws_c = torch.empty(frob.workspace_bytes("cplx_lu_inv", n, 1) + 256, dtype=torch.uint8, device=dev)
     xb = torch.empty_like(m_dev)
 
@@ -822,6 +877,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "inversions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "arithmetic": "FP64 results; products of at least 256 in every dimension as exact BF16 digit products on "
+                      "the tensor cores (FP64-accurate), factorizations and the rest on the FP64 pipe",
         "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "s": S_ROT,
                    "construction": "A = I, B = Q blockdiag([[0,-s],[s,0]]) Q^T, Q Haar orthogonal (Sec. 3)",
                    "l2": "input (1.07 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
@@ -834,9 +891,17 @@ def main():
                          "forward_error_vs_closed_form": fe_b, "residual_fro_sampled": res_b,
                          "top_kernels": dict(list(_kernels(prof_b).items())[:5])},
         "speedup_vs_cplx_lu": tb_ms / ms_per_step,
+        "frob_inv_fp64_pipe": {"value": world / (tp_ms * 1e-3), "unit": "inversions/s", "ms_per_step": tp_ms,
+                               "steps": kb, "tflops_executed": exec_f / (tp_ms * 1e-3) / 1e12,
+                               "forward_error_vs_closed_form": fe_p, "residual_fro_sampled": res_p,
+                               "speedup_vs_cplx_lu": tb_ms / tp_ms,
+                               "what": "the same algorithm with every product on the FP64 pipe (gemm=fp64_pipe)",
+                               "roofline": _roofline(prof_p, clocks),
+                               "top_kernels": dict(list(_kernels(prof_p).items())[:5])},
         "flops_note": "executed 26 n^3/3 (Frobenius) vs 8 n^3 (complex LU, identity right-hand side exploited); "
                       "the paper's counts are 28 n^3/3 vs 32 n^3/3 (Sec. 4.1)",
         "roofline": roof,
+        "roofline_tensor": _roofline_digits(prof),
         "path_roofline": {"bound": "alu", "achieved": exec_f / (ms_per_step * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                           "unit": "TFLOP/s", "frac": exec_f / (ms_per_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                           "what": "whole step, executed FP64 flops"},

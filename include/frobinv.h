@@ -101,8 +101,18 @@ typedef struct {
                           whose U has the larger min |u_kk| / max |u_kk| is
                           used (a singular factor counts as 0).  Not with
                           almost_sure. */
-  int32_t reserved;    /* must be 0 */
-} frob_opts;           /* NULL => {FROB_FP64, 0, 0, 0, 8, 1e-14, FROB_PART_A, 0} */
+  int32_t fp64_gemm;   /* FROB_FP64 only (frob_gemm): how the large real
+                          products run.  FROB_GEMM_AUTO: products of at least
+                          256 in every dimension as exact digit products on
+                          the BF16 tensor cores (FP64-accurate: each operand
+                          row / column scaled by a power of two and split into
+                          eight 7-bit digits, digit products exact in FP32
+                          over K chunks of 512, summed exactly in 64-bit fixed
+                          point); FROB_GEMM_FP64_PIPE: every product on the
+                          FP64 pipe.  Other values: FROB_ERR_ARG. */
+} frob_opts;           /* NULL => {FROB_FP64, 0, 0, 0, 8, 1e-14, FROB_PART_A, FROB_GEMM_AUTO} */
+
+typedef enum { FROB_GEMM_AUTO = 0, FROB_GEMM_FP64_PIPE = 1 } frob_gemm;
 
 typedef enum { FROB_PART_A = 0, FROB_PART_B = 1, FROB_PART_AUTO = 2 } frob_part;
 
@@ -213,9 +223,11 @@ frob_status cplx_inv_mixed(int op, int n, int batch, const void* M, int64_t ldm,
  *
  * Arguments and results are those of frob_inv_hpd with prec = FROB_FP64.
  * The problem must fit the scratch: frob_workspace_bytes(FROB_OP_INV_HPD, n,
- * batch, FROB_FP64) <= 32 MiB, i.e. about n * n * batch <= 2^20 (n = 1024 with
- * batch 1, n = 512 with batch 4); larger problems return FROB_ERR_WORKSPACE
- * and launch nothing.  Other argument errors return FROB_ERR_ARG.
+ * batch, FROB_FP64) <= 32 MiB, about 64 n^2 batch bytes (four FP64 planes and,
+ * from n = 256 on, the digits of the final product), i.e. n * n * batch up to
+ * about 5e5 (n = 512 with batch 1, n = 256 with batch 7); larger problems
+ * return FROB_ERR_WORKSPACE and launch nothing.  Other argument errors return
+ * FROB_ERR_ARG.
  *
  * The first call made with a given device current looks up the scratch
  * array's device address on that device and keeps it for the life of the

@@ -319,7 +319,8 @@ frob_status frob_inv(int n, int batch, const void* M, int64_t ldm, int64_t sm, v
                      const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
   frob_opts o = opts ? *opts : default_opts();
   if (o.almost_sure != 0 && o.almost_sure != 1) return FROB_ERR_ARG;
-  if (o.part < FROB_PART_A || o.part > FROB_PART_AUTO || o.reserved != 0) return FROB_ERR_ARG;
+  if (o.part < FROB_PART_A || o.part > FROB_PART_AUTO) return FROB_ERR_ARG;
+  if (o.fp64_gemm != FROB_GEMM_AUTO && o.fp64_gemm != FROB_GEMM_FP64_PIPE) return FROB_ERR_ARG;
   if (o.part != FROB_PART_A && o.almost_sure) return FROB_ERR_ARG;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_INV, n, batch, o.prec), info, o.prec);
@@ -363,6 +364,7 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
                          const frob_opts* opts, void* ws, size_t wsb, frob_info* info, void* stream) {
   frob_opts o = opts ? *opts : default_opts();
   if (o.almost_sure) return FROB_ERR_ARG;  // A is SPD for HPD input (Lemma "positive real part")
+  if (o.fp64_gemm != FROB_GEMM_AUTO && o.fp64_gemm != FROB_GEMM_FP64_PIPE) return FROB_ERR_ARG;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb,
                                frob_workspace_bytes(FROB_OP_INV_HPD, n, batch, o.prec), info, o.prec);
   if (s != FROB_OK) return s;
@@ -389,7 +391,7 @@ frob_status frob_inv_hpd(int n, int batch, const void* M, int64_t ldm, int64_t s
                            w, info + first, s2);
     else
       frob_chol_run<double>(n, count, in_view<zd>(M, ldm, sm).at_batch(first), out_view<zd>(X, ldx, sx).at_batch(first),
-                            w, info + first, s2);
+                            w, info + first, s2, o.fp64_gemm);
   }, &key, wsb);
   return launched();
 }
@@ -399,7 +401,7 @@ frob_status cplx_inv_mixed(int op, int n, int batch, const void* M, int64_t ldm,
   if (op != FROB_OP_CPLX_LU && op != FROB_OP_CPLX_CHOL) return FROB_ERR_ARG;
   frob_opts o = opts ? *opts : default_opts();
   if (!opts) o.prec = FROB_MIXED_BF16;
-  if (o.almost_sure || o.part != FROB_PART_A || o.reserved != 0) return FROB_ERR_ARG;
+  if (o.almost_sure || o.part != FROB_PART_A || o.fp64_gemm != FROB_GEMM_AUTO) return FROB_ERR_ARG;
   frob_status s = check_common(n, batch, M, ldm, sm, X, ldx, sx, ws, wsb, frob_workspace_bytes(op, n, batch, o.prec),
                                info, o.prec);
   if (s != FROB_OK) return s;

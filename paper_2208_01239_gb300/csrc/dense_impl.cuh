@@ -660,8 +660,12 @@ template <typename T> constexpr size_t laswp_trsm_smem() {
   return sizeof(T) * (size_t)(PANEL_MAX * (PANEL_MAX + 1) + PANEL_MAX * (TB + 1));
 }
 
+// u_end: U12 is formed for the columns [k0 + kb, u_end) only (n for the
+// whole row; a recursive LU's block passes its right edge); the swaps reach
+// every column outside the panel.
 template <typename T>
-__global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, MatB<T> A, const int* piv) {
+__global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, MatB<T> A, const int* piv,
+                                                         int u_end) {
   const int b = blockIdx.z;
   const int t = threadIdx.x;
   const int c0 = blockIdx.x * TB;
@@ -683,7 +687,7 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
       }
     }
   }
-  if (c0 + TB <= k0 + kb) return;  // strip entirely left of / inside the panel
+  if (c0 + TB <= k0 + kb || c0 >= u_end) return;  // strip left of / inside the panel, or right of the block
   __syncthreads();
   for (int e = t; e < kb * kb; e += NTH) {
     int r = e / kb, q = e % kb;
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
   for (int e = t; e < kb * TB; e += NTH) {
     int r = e / TB, q = e % TB;
     int cc = c0 + q;
-    u[r * US + q] = (cc < n && cc >= k0 + kb) ? Ab[(int64_t)(k0 + r) * A.ld + cc] : zero_v<T>();
+    u[r * US + q] = (cc < u_end && cc >= k0 + kb) ? Ab[(int64_t)(k0 + r) * A.ld + cc] : zero_v<T>();
   }
   __syncthreads();
   // forward substitution with the unit lower triangle L11, one column per thread
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(NTH) laswp_trsm_kernel(int n, int k0, int kb, 
   for (int e = t; e < kb * TB; e += NTH) {
     int r = e / TB, q = e % TB;
     int cc = c0 + q;
-    if (cc < n && cc >= k0 + kb) Ab[(int64_t)(k0 + r) * A.ld + cc] = u[r * US + q];
+    if (cc < u_end && cc >= k0 + kb) Ab[(int64_t)(k0 + r) * A.ld + cc] = u[r * US + q];
   }
 }
 

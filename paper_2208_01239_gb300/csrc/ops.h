@@ -51,7 +51,7 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
 template <typename R> size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out);
 template <typename R>
 void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
-                   void* ws, frob_info* info, cudaStream_t st);
+                   void* ws, frob_info* info, cudaStream_t st, int fp64_gemm = FROB_GEMM_AUTO);
 template <typename C> size_t cplx_lu_ws(int n, int batch, void* ws, CPlanes<C>* out);
 template <typename C> void cplx_lu_run(int n, int batch, MatB<const C> M, MatB<C> X, void* ws, frob_info* info,
                                        cudaStream_t st);

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "dense_impl.cuh"
 #include "ops.h"
+#include "ozr.cuh"
 #include "tc_gemm.cuh"
 
 namespace frob {
@@ -185,6 +186,12 @@ struct TcScratch {
   int* err = nullptr;
 };
 inline thread_local TcScratch t_tc;
+// The same for the FP64 drivers: FP64 products of at least ozr::MIN_MNK in
+// every dimension run as exact digit products on the BF16 tensor cores
+// (ozr.cuh) while an OzScope is open.
+inline thread_local TcScratch t_oz;
+inline TcScratch& tc_slot() { return t_tc; }
+inline TcScratch& oz_slot() { return t_oz; }
 
 
 static __global__ void tc_err_report_kernel(const int* err, frob_info* info, int batch) {
@@ -192,25 +199,25 @@ static __global__ void tc_err_report_kernel(const int* err, frob_info* info, int
   if (b < batch && *err != 0) report(info, b, FROB_ERR_TIMEOUT, 0);
 }
 
-class TcScope {
+template <TcScratch& (*SLOT)()> class ScratchScope {
  public:
-  TcScope(unsigned char* p, size_t bytes, frob_info* info, int batch, cudaStream_t st)
-      : saved_(t_tc), info_(info), batch_(batch), st_(st) {
-    if (p && bytes > 256 && !t_tc_off) {
-      t_tc = TcScratch{p, bytes, reinterpret_cast<int*>(p)};
+  ScratchScope(unsigned char* p, size_t bytes, frob_info* info, int batch, cudaStream_t st, bool on = true)
+      : saved_(SLOT()), info_(info), batch_(batch), st_(st) {
+    if (on && p && bytes > 256 && !t_tc_off) {
+      SLOT() = TcScratch{p, bytes, reinterpret_cast<int*>(p)};
       cudaMemsetAsync(p, 0, 256, st);
     } else {
-      t_tc = TcScratch{};
+      SLOT() = TcScratch{};
     }
   }
-  ~TcScope() {
-    if (t_tc.err && info_)
+  ~ScratchScope() {
+    if (SLOT().err && info_)
       FROB_LAUNCH("tc_err_report", st_,
-                  tc_err_report_kernel<<<(batch_ + 127) / 128, 128, 0, st_>>>(t_tc.err, info_, batch_));
-    t_tc = saved_;
+                  tc_err_report_kernel<<<(batch_ + 127) / 128, 128, 0, st_>>>(SLOT().err, info_, batch_));
+    SLOT() = saved_;
   }
-  TcScope(const TcScope&) = delete;
-  TcScope& operator=(const TcScope&) = delete;
+  ScratchScope(const ScratchScope&) = delete;
+  ScratchScope& operator=(const ScratchScope&) = delete;
 
  private:
   TcScratch saved_;
@@ -218,6 +225,13 @@ class TcScope {
   int batch_;
   cudaStream_t st_;
 };
+using TcScope = ScratchScope<tc_slot>;
+using OzScope = ScratchScope<oz_slot>;
+
+// bytes an FP64 driver reserves for its largest digit product (order n)
+inline size_t oz_scratch_for(int n, int batch) {
+  return n >= ozr::MIN_MNK ? ozr::scratch_bytes(n, n, n, batch) : 0;
+}
 
 template <typename T, int OPA, int OPB, class Epi>
 inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<const T> B, Epi epi, int tile_mode,
@@ -234,6 +248,20 @@ inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<co
                           &mb, st)) {
         set_launch_flops(fl);
         tc::tc3_launch(ma, mb, M, N, K, batch, epi, t_tc.err, st);
+        return;
+      }
+    }
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (tile_mode == 0 && npairs == 1 && t_oz.p && M >= ozr::MIN_MNK && N >= ozr::MIN_MNK && K >= ozr::MIN_MNK &&
+        ozr::scratch_bytes(M, N, K, batch) <= t_oz.bytes) {
+      CUtensorMap ma, mb;
+      ozr::RArgs ra;
+      // op(B)'s columns are the rows of B when OPB transposes it
+      if (ozr::prepare(M, N, K, batch, A.p, A.ld, A.bs, OPA != OP_N, B.p, B.ld, B.bs, OPB != OP_N, t_oz.p, t_oz.err,
+                       &ma, &mb, &ra, st)) {
+        set_launch_flops(fl);
+        ozr::launch(ma, mb, ra, epi, st);
         return;
       }
     }
@@ -368,6 +396,22 @@ inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cu
   // the pairs of one level with full-size C in one launch (pair p is pair 0
   // moved 2 s p down the diagonal), a short last pair on its own
   auto join = [&](int r, int s, int sc, int npairs) {
+    if constexpr (std::is_same<T, double>::value) {
+      // with the FP64 digit products on: each pair as two full products on
+      // the tensor cores (the zero triangles included), one pair per launch
+      if (t_oz.p && s >= ozr::MIN_MNK && sc >= ozr::MIN_MNK) {
+        for (int q = 0; q < npairs; ++q) {
+          const int rq = r + 2 * s * q;
+          MatB<T> Tq = Tmp.sub(rq + s, rq);
+          gemm_launch<T, OP_N, OP_N>(sc, s, s, batch, Lm.sub(rq + s, rq), cst(X.sub(rq, rq)),
+                                     axpby<T>(Tq, one_v<T>(), zero_v<T>(), true), 0, st);       // B A^{-1}
+          gemm_launch<T, OP_N, OP_N>(sc, s, sc, batch, cst(X.sub(rq + s, rq + s)), cst(Tq),
+                                     axpby<T>(X.sub(rq + s, rq), neg_(one_v<T>()), zero_v<T>(), true), 0,
+                                     st);                                                         // -C^{-1} (B A^{-1})
+        }
+        return;
+      }
+    }
     MatB<const T> B = Lm.sub(r + s, r);
     MatB<T> Tp = Tmp.sub(r + s, r);
     gemm_launch<T, OP_N, OP_N>(sc, s, s, batch, B, cst(X.sub(r, r)), axpby<T>(Tp, one_v<T>(), zero_v<T>(), true), 4,
@@ -417,33 +461,17 @@ template <typename T> inline const char* getrf_mc_name() {
   return s.c_str();
 }
 
-// Blocked right-looking LU with partial pivoting (P A = L U, in place).
-// Panels of more than PANEL_THREADS rows are factored by several cooperating
-// CTAs per matrix when `mcs` (mc_scratch_bytes of scratch) is given: one
-// cooperative launch of G x batch CTAs, G x batch at most one per SM, so a
-// single large matrix keeps the panel off its critical path's single SM.
+// Panels [kbeg, kend) of a right-looking LU with partial pivoting, in place:
+// each 32-wide panel is factored (by cooperating CTAs when `mc`), its row
+// exchanges are applied to every other column of the matrix, and U12 and the
+// trailing update reach the columns up to u_end (n: the whole matrix; a
+// recursive LU's block passes its right edge).
 template <typename T>
-inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
-                  unsigned char* mcs = nullptr) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (n <= SLU_MAX) {
-      // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
-      set_smem_attr(getrf_small_kernel<float>, SLU_SMEM);
-      FROB_LAUNCH("getrf_small<f32>", st,
-                  getrf_small_kernel<float><<<batch, SLU_THREADS, SLU_SMEM, st>>>(n, A, piv, info, info_off));
-      return;
-    }
-  }
-  panel_smem_attr<T>();
-  const bool mc = mcs != nullptr && mc_scratch_bytes<T>(n, batch) > 0;
-  const int gcap = mc ? std::max(1, std::min(MC_GMAX, num_sms() / batch)) : 0;
-  if (mc) {
-    set_smem_attr(getrf_panel_mc_kernel<T>, (int)MC_SMEM_MAX);
-    cudaMemsetAsync(mcs, 0, mc_scratch_bytes<T>(n, batch), st);  // barrier counters and flags
-  }
+inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
+                         unsigned char* mcs, bool mc, int gcap, int kbeg, int kend, int u_end) {
   const int nb = panel_width<T>();
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int kb = std::min(nb, n - k0);
+  for (int k0 = kbeg; k0 < kend; k0 += nb) {
+    const int kb = std::min(nb, kend - k0);
     const int m = n - k0;
     const size_t bytes = (size_t)m * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
@@ -470,16 +498,85 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
                   getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info,
                                                                                          info_off, staged));
     }
-    FROB_LAUNCH(laswp_name<T>(), st, laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A, piv));
+    FROB_LAUNCH(laswp_name<T>(), st,
+                laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A,
+                                                                                                       piv, u_end));
     const int r = k0 + kb;
-    if (r < n) {
+    if (r < u_end) {
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
       MatB<const T> U12{A.p + (int64_t)k0 * A.ld + r, A.ld, A.bs};
       MatB<T> A22 = A.sub(r, r);
-      gemm_launch<T, OP_N, OP_N>(n - r, n - r, kb, batch, L21, U12, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
-                                 0, st);
+      gemm_launch<T, OP_N, OP_N>(n - r, u_end - r, kb, batch, L21, U12,
+                                 axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false), 0, st);
     }
   }
+}
+
+// Recursive LU of the column block [c0, c0 + w) (rows c0 .. n - 1; Toledo's
+// recursion, as LAPACK's getrf2): factor the left half, U12 = L11^{-1} A12
+// (a triangular solve), A22 -= L21 U12 (one product with K = the left
+// half's width), factor the right half.  The row exchanges are applied to
+// every column as each panel is factored, so the halves need no separate
+// exchange passes.  Blocks of at most GETRF_REC_NB columns take the panel
+// loop.  With the tensor-core products on, every product of the recursion
+// has K >= 1024 and runs on the tensor cores (the panel loop's rank-32
+// updates stay on the CUDA cores), and every U12 solve has at least 1024
+// rows and takes the recursive form; narrower blocks would hand their U12 to
+// block-row solves of a few CTAs each (measured: 112 ms of a 521 ms
+// inversion of order 8192 with 512-wide blocks).
+constexpr int GETRF_REC_NB = 2048;
+constexpr int GETRF_REC_MIN = GETRF_REC_NB + 1;  // smallest order that takes the recursion
+
+template <typename T>
+inline void getrf_rec(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
+                      unsigned char* mcs, bool mc, int gcap, int c0, int w) {
+  if (w <= GETRF_REC_NB) {
+    getrf_panels<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0, c0 + w, c0 + w);
+    return;
+  }
+  const int w1 = ((w / 2 + 255) / 256) * 256;  // a multiple of 256, at least 1024 here
+  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0, w1);
+  auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
+  MatB<T> A12 = A.sub(c0, c0 + w1);
+  trsm_any<T, OP_N, true, true>(w1, w - w1, batch, cst(A.sub(c0, c0)), cst(A12), A12, nullptr, st);
+  gemm_launch<T, OP_N, OP_N>(n - c0 - w1, w - w1, w1, batch, cst(A.sub(c0 + w1, c0)), cst(A12),
+                             axpby<T>(A.sub(c0 + w1, c0 + w1), neg_(one_v<T>()), one_v<T>(), false), 0, st);
+  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0 + w1, w - w1);
+}
+
+// LU with partial pivoting (P A = L U, in place).  Panels of more than
+// PANEL_THREADS rows are factored by several cooperating CTAs per matrix when
+// `mcs` (mc_scratch_bytes of scratch) is given: one cooperative launch of
+// G x batch CTAs, G x batch at most one per SM, so a single large matrix keeps
+// the panel off its critical path's single SM.  Orders from GETRF_REC_MIN on
+// take the recursive form while tensor-core products are on (FP64 digit
+// products or FP32 split TF32), the right-looking panel loop otherwise.
+template <typename T>
+inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
+                  unsigned char* mcs = nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (n <= SLU_MAX) {
+      // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
+      set_smem_attr(getrf_small_kernel<float>, SLU_SMEM);
+      FROB_LAUNCH("getrf_small<f32>", st,
+                  getrf_small_kernel<float><<<batch, SLU_THREADS, SLU_SMEM, st>>>(n, A, piv, info, info_off));
+      return;
+    }
+  }
+  panel_smem_attr<T>();
+  const bool mc = mcs != nullptr && mc_scratch_bytes<T>(n, batch) > 0;
+  const int gcap = mc ? std::max(1, std::min(MC_GMAX, num_sms() / batch)) : 0;
+  if (mc) {
+    set_smem_attr(getrf_panel_mc_kernel<T>, (int)MC_SMEM_MAX);
+    cudaMemsetAsync(mcs, 0, mc_scratch_bytes<T>(n, batch), st);  // barrier counters and flags
+  }
+  bool rec = false;
+  if constexpr (std::is_same<T, double>::value) rec = t_oz.p != nullptr;
+  if constexpr (std::is_same<T, float>::value) rec = t_tc.p != nullptr;
+  if (rec && n >= GETRF_REC_MIN)
+    getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, 0, n);
+  else
+    getrf_panels<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, 0, n, n);
 }
 
 // Blocked right-looking Cholesky (A = L L^H, lower triangle, in place): per
@@ -560,7 +657,9 @@ size_t frob_lu_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.partb = c.take<int>((size_t)batch);
   p.infoB = c.take<frob_info>((size_t)batch);
   p.mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n, batch));
-  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0;
+  // FP32: split-TF32 tensor-core products; FP64: digit products on the BF16
+  // tensor cores (the same slot; only one applies per precision)
+  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : oz_scratch_for(n, batch);
   p.tcs = c.take<unsigned char>(p.tcs_bytes);
   if (out) *out = p;
   return c.off;
@@ -637,7 +736,11 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
                  const frob_opts& o, void* ws, frob_info* info, cudaStream_t st) {
   Planes<R> p;
   frob_lu_ws<R>(n, batch, ws, &p);
-  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st);  // FP32: large products on the tensor cores
+  // large products on the tensor cores: split TF32 (FP32), exact BF16 digit
+  // products (FP64, unless opts ask for the FP64 pipe)
+  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st, std::is_same<R, float>::value);
+  OzScope oz_scope(p.tcs, p.tcs_bytes, info, batch, st,
+                   std::is_same<R, double>::value && o.fp64_gemm == FROB_GEMM_AUTO);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   const bool autop = o.part == FROB_PART_AUTO;
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, o.almost_sure, o.seed,
@@ -677,7 +780,7 @@ size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out) {
   p.S = plane<R>(c, n, batch);
   p.Bp = plane<R>(c, n, batch);
   p.Y = plane<R>(c, n, batch);
-  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : 0;
+  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : oz_scratch_for(n, batch);
   p.tcs = c.take<unsigned char>(p.tcs_bytes);
   if (out) *out = p;
   return c.off;
@@ -685,10 +788,14 @@ size_t frob_chol_ws(int n, int batch, void* ws, Planes<R>* out) {
 
 template <typename R>
 void frob_chol_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB<typename cplx_of<R>::type> X,
-                   void* ws, frob_info* info, cudaStream_t st) {
+                   void* ws, frob_info* info, cudaStream_t st, int fp64_gemm) {
   Planes<R> p;
   frob_chol_ws<R>(n, batch, ws, &p);
-  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st);  // FP32: large products on the tensor cores
+  // large products on the tensor cores: split TF32 (FP32), exact BF16 digit
+  // products (FP64, unless the caller asks for the FP64 pipe)
+  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st, std::is_same<R, float>::value);
+  OzScope oz_scope(p.tcs, p.tcs_bytes, info, batch, st,
+                   std::is_same<R, double>::value && fp64_gemm == FROB_GEMM_AUTO);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 1, 0, 0, 0));
   potrf<R>(n, batch, p.LA, info, 0, st);                                                 // A = R1^T R1, L1 = R1^T

@@ -50,7 +50,7 @@ assert INFO_DTYPE.itemsize == 32
 class FrobOpts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("almost_sure", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("attempt", ctypes.c_int32), ("ns_max_iter", ctypes.c_int32), ("ns_tol", ctypes.c_double),
-                ("part", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("part", ctypes.c_int32), ("fp64_gemm", ctypes.c_int32)]
 
 
 PART = {"A": 0, "B": 1, "auto": 2}
@@ -279,10 +279,14 @@ def _call(op: str, m: torch.Tensor, prec: str, opts: FrobOpts | None, out: torch
     return res
 
 
+GEMM = {"auto": 0, "fp64_pipe": 1}
+
+
 def _opts(prec: str, almost_sure: bool = False, seed: int = 0, attempt: int = 0, ns_tol: float = 1e-14,
-          ns_max_iter: int = 8, part: str = "A") -> FrobOpts:
+          ns_max_iter: int = 8, part: str = "A", gemm: str = "auto") -> FrobOpts:
     o = FrobOpts()
     o.part = PART[part]
+    o.fp64_gemm = GEMM[gemm]
     o.prec = PREC[prec]
     o.almost_sure = 1 if almost_sure else 0
     o.seed = seed
@@ -294,23 +298,27 @@ def _opts(prec: str, almost_sure: bool = False, seed: int = 0, attempt: int = 0,
 
 def frob_inv(m: torch.Tensor, prec: str = "fp64", almost_sure: bool = False, seed: int = 0, attempt: int = 0,
              out=None, ws=None, info=None, check: bool = True, ns_tol: float = 1e-14, ns_max_iter: int = 8,
-             part: str = "A") -> Result:
+             part: str = "A", gemm: str = "auto") -> Result:
     """(A + iB)^{-1} = S^{-1} - i A^{-1} B S^{-1}, S = A + B A^{-1} B.
 
     part: "A" (the formula above), "B" (the formula for invertible B,
     B^{-1}A(AB^{-1}A + B)^{-1} - i(AB^{-1}A + B)^{-1}, Sec. 4.2) or "auto"
     (per matrix, the real part whose LU has the larger pivot ratio).
+    gemm (FP64): "auto" runs products of at least 256 in every dimension as
+    exact digit products on the BF16 tensor cores, "fp64_pipe" keeps every
+    product on the FP64 pipe.
     ns_tol / ns_max_iter: stopping rule of the mixed precisions' Newton-Schulz
     refinement (relative residual ||I - M X||_F / (||M||_F ||X||_F))."""
-    return _call("frob_inv", m, prec, _opts(prec, almost_sure, seed, attempt, ns_tol, ns_max_iter, part), out, ws,
-                 info, check)
+    return _call("frob_inv", m, prec, _opts(prec, almost_sure, seed, attempt, ns_tol, ns_max_iter, part, gemm), out,
+                 ws, info, check)
 
 
 def frob_inv_hpd(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True,
-                 ns_tol: float = 1e-14, ns_max_iter: int = 8) -> Result:
+                 ns_tol: float = 1e-14, ns_max_iter: int = 8, gemm: str = "auto") -> Result:
     """Frobenius inversion with two real Cholesky factorisations (HPD input,
-    lower triangle read)."""
-    return _call("frob_inv_hpd", m, prec, _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter), out, ws, info, check)
+    lower triangle read); gemm as for frob_inv."""
+    return _call("frob_inv_hpd", m, prec, _opts(prec, ns_tol=ns_tol, ns_max_iter=ns_max_iter, gemm=gemm), out, ws,
+                 info, check)
 
 
 def cplx_lu_inv(m: torch.Tensor, prec: str = "fp64", out=None, ws=None, info=None, check: bool = True,

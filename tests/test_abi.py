@@ -44,7 +44,11 @@ def test_host_only_calls(lib):
     assert lib.frob_workspace_bytes(0, 0, 1, 0) == 0
     assert lib.frob_workspace_bytes(9, 16, 1, 0) == 0
     # fp32 planes are half the size of fp64 planes
-    assert lib.frob_workspace_bytes(1, 512, 4, 1) < lib.frob_workspace_bytes(1, 512, 4, 0)
+    # FP32 planes are half the size (below order 256, where FP32 products
+    # need no split-TF32 scratch)
+    assert lib.frob_workspace_bytes(1, 128, 4, 1) < lib.frob_workspace_bytes(1, 128, 4, 0)
+    # the FP64 general route reserves the digit-product scratch from order 256 on
+    assert lib.frob_workspace_bytes(0, 256, 1, 0) > lib.frob_workspace_bytes(0, 255, 1, 0) + 2 * 8 * 256 * 256 * 2
     lib.frob_status_str.restype = ctypes.c_char_p
     assert lib.frob_status_str(2) == b"FROB_ERR_SINGULAR"
     # argument errors return synchronously, before any launch
@@ -62,12 +66,12 @@ def test_host_only_calls(lib):
 
 def test_opts_layout_matches_the_binding():
     """frob_opts is 40 bytes (prec, almost_sure, seed, attempt, ns_max_iter,
-    ns_tol, part, reserved); the binding's ctypes mirror has the same size
+    ns_tol, part, fp64_gemm); the binding's ctypes mirror has the same size
     and offsets."""
     from paper_2208_01239_gb300 import frob
     o = frob.FrobOpts
     assert ctypes.sizeof(o) == 40
-    assert [o.seed.offset, o.ns_tol.offset, o.part.offset, o.reserved.offset] == [8, 24, 32, 36]
+    assert [o.seed.offset, o.ns_tol.offset, o.part.offset, o.fp64_gemm.offset] == [8, 24, 32, 36]
 
 
 def test_host_only_checks_of_the_newer_entry_points(lib):
@@ -77,12 +81,12 @@ def test_host_only_checks_of_the_newer_entry_points(lib):
     from paper_2208_01239_gb300 import frob
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
     L = ctypes.CDLL(frob.library_path())
-    # frob_inv: part out of range, reserved set, part with the almost sure option
+    # frob_inv: part out of range, an unknown fp64_gemm, part with the almost sure option
     L.frob_inv.restype = i32
     L.frob_inv.argtypes = [i32, i32, vp, i64, i64, vp, i64, i64, ctypes.POINTER(frob.FrobOpts), vp, sz, vp, vp]
-    for part, reserved, almost in ((3, 0, 0), (0, 1, 0), (1, 0, 1), (2, 0, 1)):
+    for part, gemm, almost in ((3, 0, 0), (0, 2, 0), (0, -1, 0), (1, 0, 1), (2, 0, 1)):
         o = frob._opts("fp64", part="A")
-        o.part, o.reserved, o.almost_sure = part, reserved, almost
+        o.part, o.fp64_gemm, o.almost_sure = part, gemm, almost
         assert L.frob_inv(4, 1, 16, 4, 16, 4096, 4, 16, ctypes.byref(o), 256, 1 << 20, 512, None) == 1
     # workspace sizes
     L.frob_newton_workspace_bytes.restype = sz
@@ -151,7 +155,7 @@ def test_bindings_reject_bad_inputs_before_calling_the_library():
         frob._opts("fp64", part="C")
     assert frob.ROUTE == {"frob": 0, "cplx_lu": 1} and frob.PART == {"A": 0, "B": 1, "auto": 2}
     o = frob._opts("fp32", part="auto")
-    assert (o.prec, o.part, o.reserved, o.almost_sure) == (frob.PREC["fp32"], 2, 0, 0)
+    assert (o.prec, o.part, o.fp64_gemm, o.almost_sure) == (frob.PREC["fp32"], 2, 0, 0)
 
 
 def test_batched_plan_sizes(lib):

@@ -385,6 +385,38 @@ def test_nan_input_reported(F):
     assert info["status"][0] == F.FROB_OK and info["status"][1] == F.FROB_ERR_SINGULAR
 
 
+@pytest.mark.parametrize("where", ["real", "imag"])
+def test_nan_input_reported_at_digit_product_sizes(F, where):
+    """n = 300: S = A + B X1 and the last product run as digit products on the
+    tensor cores.  A NaN in the imaginary part never reaches a pivot of A, so
+    the digit path must carry it through S (a row or column with a non-finite
+    entry gives NaN products, as on the FP64 pipe) for the LU of S to report
+    it; a NaN in the real part is caught by the LU of A."""
+    m = W.gaussian(300, 2, seed=19)
+    if where == "real":
+        m[1, 4, 7] = np.nan + 1j * m[1, 4, 7].imag
+    else:
+        m[1, 4, 7] = m[1, 4, 7].real + 1j * np.nan
+    info = F.frob_inv(_dev(m), check=False).info()
+    assert info["status"][0] == F.FROB_OK and info["status"][1] == F.FROB_ERR_SINGULAR
+
+
+@pytest.mark.parametrize("n", [256, 300, 640, 1030])
+def test_digit_products_match_fp64_pipe(F, n):
+    """FP64 products of at least 256 in every dimension run as exact BF16
+    digit products (eight 7-bit digits per scaled entry) by default; against
+    the same algorithm with every product on the FP64 pipe and against the
+    oracle, both within the route's gate (ten times the oracle route's own
+    error against LAPACK)."""
+    m = W.gaussian(n, 1, seed=5400 + n)[0]
+    xa = F.frob_inv(_dev(m)).x.cpu().numpy()
+    xp = F.frob_inv(_dev(m), gemm="fp64_pipe").x.cpu().numpy()
+    gate = _route_bound(m, "frob")
+    assert metrics.forward_error(xa, oracle.frob_inv_lu(m)) <= gate
+    assert metrics.forward_error(xa, xp) <= gate
+    assert metrics.residual_fro(m, xa) <= RES_GATE["fp64"]
+
+
 def test_not_hpd_reported(F):
     ms = W.hpd(16, 3, seed=10)
     ms[1] = ms[1] - 2 * np.abs(np.linalg.eigvalsh(ms[1])).max() * np.eye(16)  # indefinite

@@ -127,7 +127,7 @@ def test_part_argument_errors(F):
         F.frob_inv(m, almost_sure=True, part="B")
     assert e.value.status == F.FROB_ERR_ARG
     o = F._opts("fp64")
-    o.reserved = 1
+    o.fp64_gemm = 5
     with pytest.raises(F.FrobError) as e:
         F._call("frob_inv", m, "fp64", o, None, None, None, True)
     assert e.value.status == F.FROB_ERR_ARG

@@ -36,6 +36,9 @@ def test_profile_flops_match_executed_count(F, op, alg, n):
     # uncounted: the panels and the U12 solves beside them (about 2 x 32 n^2
     # flops each per factorization) and the triangular inverses' 64 x 64
     # diagonal blocks; counted beyond the leading order: whole 64 x 64 tiles
-    # on the diagonals of the triangular products
-    assert 0.90 * want <= counted <= 1.03 * want, (counted / want, rep)
+    # on the diagonals of the triangular products, and, in FP64 from order
+    # 256 on, the zero triangles of the triangular inverse's joins, which run
+    # as full products on the tensor cores (at most n^3 / 3 more)
+    hi = 1.03 if (alg != "frob_lu" or n < 256) else 1.03 + (1 / 3) / float(flops.EXECUTED[alg])
+    assert 0.90 * want <= counted <= hi * want, (counted / want, rep)
     assert all(v[1] > 0 for v in rep.values())

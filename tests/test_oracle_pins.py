@@ -406,3 +406,20 @@ def test_bench_roofline_arithmetic():
     assert abs(r["frac"] - r["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
     assert abs(r["peak_at_sampled_clock"] - bench.FP64_PEAK_TFLOPS / 2) < 1e-9
     assert abs(r["share_of_step"] - 30.0 / 42.0) < 1e-12
+
+
+def test_bench_roofline_digit_products():
+    """When the FP64 digit-product GEMM dominates, the roofline is the tensor
+    pipe's: its FP64 flops times the 36 BF16 digit products each takes,
+    against the BF16 peak."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    prof = {"ozr_gemm<f64 digits>": (10.0, 100.0, 2.0e12), "gemm<f64,op0,op0,axpby>": (5.0, 50.0, 5e10)}
+    r = bench._roofline(prof, {"sm_mhz": 2070.0})
+    assert r["bound"] == "tensor" and r["kernel"] == "ozr_gemm<f64 digits>"
+    assert abs(r["achieved"] - 36 * 2.0e12 / 0.1 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
