@@ -630,10 +630,18 @@ def measure_accuracy(frob, dev):
         # S = A + B A^{-1} B, complex LU with M; the gap between the two
         # routes' left residuals set against kappa(S) / kappa(M)
         a, b = m.real, m.imag
-        sm = a + b @ np.linalg.solve(a, b)
+        x1 = np.linalg.solve(a, b)
+        bx1 = b @ x1
+        sm = a + bx1
+        sinv = np.linalg.inv(sm)
         km, ka, ks = (float(np.linalg.cond(t)) for t in (m, a, sm))
         row["conditioning"] = {"kappa_M": km, "kappa_A": ka, "kappa_S": ks, "kappa_S_over_kappa_M": ks / km,
-                               "res_L_frob_over_cplx_lu": row["frob_inv"]["res_L"] / row["cplx_lu_inv"]["res_L"]}
+                               "cancellation_in_S": float(np.linalg.norm(bx1) / np.linalg.norm(sm)),
+                               "growth_in_last_product": float(np.linalg.norm(x1, 2) * np.linalg.norm(sinv, 2) /
+                                                               np.linalg.norm(x1 @ sinv, 2)),
+                               "res_L_frob_over_cplx_lu": row["frob_inv"]["res_L"] / row["cplx_lu_inv"]["res_L"],
+                               "solve_error_frob_over_cplx_lu": row["frob_solve"]["forward_error"] /
+                               row["cplx_lu_solve"]["forward_error"]}
         out[f"n{n}"] = row
     return out
 
