@@ -513,47 +513,74 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
 }
 
 // Recursive LU of the column block [c0, c0 + w) (rows c0 .. n - 1; Toledo's
-// recursion, as LAPACK's getrf2): factor the left half, U12 = L11^{-1} A12
-// (a triangular solve), A22 -= L21 U12 (one product with K = the left
-// half's width), factor the right half.  The row exchanges are applied to
-// every column as each panel is factored, so the halves need no separate
-// exchange passes.  Blocks of at most GETRF_REC_NB columns take the panel
-// loop.  With the tensor-core products on, every product of the recursion
-// has K >= 1024 and runs on the tensor cores (the panel loop's rank-32
-// updates stay on the CUDA cores), and every U12 solve has at least 1024
-// rows and takes the recursive form; narrower blocks would hand their U12 to
-// block-row solves of a few CTAs each (measured: 112 ms of a 521 ms
-// inversion of order 8192 with 512-wide blocks).
+// recursion, as LAPACK's getrf2): factor the left half, U12 = L11^{-1} A12,
+// A22 -= L21 U12 (one product with K = the left half's width), factor the
+// right half.  The row exchanges are applied to every column as each panel
+// is factored, so the halves need no separate exchange passes.  Blocks of at
+// most `nb` columns take the panel loop.
+//   With an n x n scratch plane `tmp`: U12 = (L11^{-1}) A12, the inverse by the
+//   recursive triangular inverse into tmp (its joins are large products),
+//   the product into tmp and copied back; every product of the recursion then
+//   has K >= 256 and nb = GETRF_REC_NB_INV (512) keeps the panel loop's
+//   rank-32 updates on the CUDA cores small.
+//   Without it: U12 by a triangular solve, which for narrow blocks is a few
+//   CTAs of FP64-pipe work per launch, so nb = GETRF_REC_NB (2048) keeps every
+//   solve at 1024 rows or more (recursive); measured with 512-wide blocks:
+//   112 ms of a 521 ms inversion of order 8192 in those solves.
+// The left half has round_down(w / 2, 256) columns (at least 256), so the
+// inverse (w1 x w1) and its join scratch (w1 x w1, beside it) fit in tmp.
 constexpr int GETRF_REC_NB = 2048;
-constexpr int GETRF_REC_MIN = GETRF_REC_NB + 1;  // smallest order that takes the recursion
+constexpr int GETRF_REC_NB_INV = 512;
+
+template <typename T>
+__global__ void copy2d_kernel(int rows, int cols, MatB<const T> S, MatB<T> D) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  D.at(b)[(int64_t)r * D.ld + c] = S.at(b)[(int64_t)r * S.ld + c];
+}
 
 template <typename T>
 inline void getrf_rec(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
-                      unsigned char* mcs, bool mc, int gcap, int c0, int w) {
-  if (w <= GETRF_REC_NB) {
+                      unsigned char* mcs, bool mc, int gcap, int c0, int w, MatB<T> tmp, int nb) {
+  if (w <= nb) {
     getrf_panels<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0, c0 + w, c0 + w);
     return;
   }
-  const int w1 = ((w / 2 + 255) / 256) * 256;  // a multiple of 256, at least 1024 here
-  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0, w1);
+  const int w1 = tmp.p ? std::max(256, (w / 2) / 256 * 256) : ((w / 2 + 255) / 256) * 256;
+  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0, w1, tmp, nb);
   auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
   MatB<T> A12 = A.sub(c0, c0 + w1);
-  trsm_any<T, OP_N, true, true>(w1, w - w1, batch, cst(A.sub(c0, c0)), cst(A12), A12, nullptr, st);
+  if (tmp.p) {
+    MatB<T> Li = tmp, J = tmp.sub(0, w1), D = tmp.sub(0, w1);
+    trtri<T, true>(w1, batch, cst(A.sub(c0, c0)), Li, J, st);                          // L11^{-1}
+    gemm_launch<T, OP_N, OP_N>(w1, w - w1, w1, batch, cst(Li), cst(A12), axpby<T>(D, one_v<T>(), zero_v<T>(), true),
+                               0, st);                                                  // U12 = L11^{-1} A12
+    const int64_t ne = (int64_t)w1 * (w - w1);
+    FROB_LAUNCH("copy2d", st,
+                copy2d_kernel<T><<<dim3((unsigned)((ne + 255) / 256), 1, (unsigned)batch), 256, 0, st>>>(
+                    w1, w - w1, cst(D), A12));
+  } else {
+    trsm_any<T, OP_N, true, true>(w1, w - w1, batch, cst(A.sub(c0, c0)), cst(A12), A12, nullptr, st);
+  }
   gemm_launch<T, OP_N, OP_N>(n - c0 - w1, w - w1, w1, batch, cst(A.sub(c0 + w1, c0)), cst(A12),
                              axpby<T>(A.sub(c0 + w1, c0 + w1), neg_(one_v<T>()), one_v<T>(), false), 0, st);
-  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0 + w1, w - w1);
+  getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, c0 + w1, w - w1, tmp, nb);
 }
 
 // LU with partial pivoting (P A = L U, in place).  Panels of more than
 // PANEL_THREADS rows are factored by several cooperating CTAs per matrix when
 // `mcs` (mc_scratch_bytes of scratch) is given: one cooperative launch of
 // G x batch CTAs, G x batch at most one per SM, so a single large matrix keeps
-// the panel off its critical path's single SM.  Orders from GETRF_REC_MIN on
-// take the recursive form while tensor-core products are on (FP64 digit
-// products or FP32 split TF32), the right-looking panel loop otherwise.
+// the panel off its critical path's single SM.  While tensor-core products are
+// on (FP64 digit products or FP32 split TF32), orders above the recursion's
+// block width take the recursive form (with `tmp`, an n x n scratch plane:
+// U12 by triangular inverses, 512-wide blocks); the right-looking panel loop
+// otherwise.
 template <typename T>
 inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
-                  unsigned char* mcs = nullptr) {
+                  unsigned char* mcs = nullptr, MatB<T> tmp = MatB<T>{nullptr, 0, 0}) {
   if constexpr (std::is_same<T, float>::value) {
     if (n <= SLU_MAX) {
       // one CTA per matrix (panels, U12 solves and trailing updates between CTA barriers)
@@ -573,8 +600,9 @@ inline void getrf(int n, int batch, MatB<T> A, int* piv, frob_info* info, int in
   bool rec = false;
   if constexpr (std::is_same<T, double>::value) rec = t_oz.p != nullptr;
   if constexpr (std::is_same<T, float>::value) rec = t_tc.p != nullptr;
-  if (rec && n >= GETRF_REC_MIN)
-    getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, 0, n);
+  const int nb = tmp.p ? GETRF_REC_NB_INV : GETRF_REC_NB;
+  if (rec && n > nb)
+    getrf_rec<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, 0, n, tmp, nb);
   else
     getrf_panels<T>(n, batch, A, piv, info, info_off, st, mcs, mc, gcap, 0, n, n);
 }
@@ -747,11 +775,11 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
                                                        o.attempt, o.part == FROB_PART_B ? 1 : 0,
                                                        autop ? p.X1 : MatB<R>{nullptr, 0, 0}, p.partb,
                                                        autop ? p.infoB : nullptr));
-  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st, p.mcs);                                // A = P1^T L1 U1
+  getrf<R>(n, batch, p.LA, p.piv1, info, 0, st, p.mcs, p.Y);                          // A = P1^T L1 U1
   if (autop) {
     // the LU of B in the X1 plane (free until the first solve), its pivots
     // in rp1 (free until the row map is built); keep the better-conditioned
-    getrf<R>(n, batch, p.X1, p.rp1, p.infoB, 0, st, p.mcs);
+    getrf<R>(n, batch, p.X1, p.rp1, p.infoB, 0, st, p.mcs, p.Y);
     FROB_LAUNCH("choose_part", st,
                 choose_part_kernel<R><<<batch, 256, 0, st>>>(n, cst(p.LA), cst(p.X1), info, p.infoB, p.partb));
     FROB_LAUNCH("swap_part", st, swap_part_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(
@@ -762,7 +790,7 @@ void frob_lu_run(int n, int batch, MatB<const typename cplx_of<R>::type> M, MatB
   trsm_any<R, OP_N, false, false>(n, n, batch, cst(p.LA), cst(p.X1), p.X1, nullptr, st); // U1 X1 = Y
   gemm_launch<R, OP_N, OP_N>(n, n, n, batch, cst(p.Bp), cst(p.X1), axpby<R>(p.S, (R)1, (R)1, false), 0,
                              st);                                                       // S = A + B X1
-  getrf<R>(n, batch, p.S, p.piv2, info, n, st, p.mcs);                                 // S = P2^T L2 U2
+  getrf<R>(n, batch, p.S, p.piv2, info, n, st, p.mcs, p.LA);  // S = P2^T L2 U2 (L1 U1 no longer needed)
   rowperm(n, batch, p.piv2, p.rp2, st);
   trtri<R, true>(n, batch, cst(p.S), p.Y, p.LA, st);                                     // Y = L2^{-1}
   trsm_any<R, OP_N, false, false>(n, n, batch, cst(p.S), cst(p.Y), p.Y, nullptr, st); // Z = U2^{-1} Y
