@@ -280,6 +280,12 @@ frob_status frob_inv_adjoint(int n, int batch, const void* X, int64_t ldx, int64
  * entry point selected by `op` (FROB_OP_INV, FROB_OP_INV_HPD, FROB_OP_CPLX_LU
  * or FROB_OP_CPLX_CHOL) with `opts` (precision; the almost sure option is not
  * supported here).  Results and info records are scattered back.
+ * With FROB_PART_B the padding block is iI, with FROB_PART_AUTO (1 + i)I, so
+ * that the factored part of the padding is invertible; with FROB_PART_AUTO
+ * the padding's unit pivots enter the pivot ratio min |u_kk| / max |u_kk|
+ * that chooses the part, so a matrix in an uneven batch may be inverted
+ * through the other part than the same matrix alone (both are correct
+ * inverses; results may then differ in rounding).
  *
  *   n_host, n_dev   the orders, on the host (to plan the launches) and on
  *                   the device (identical contents)

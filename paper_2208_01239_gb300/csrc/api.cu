@@ -139,15 +139,31 @@ frob_status launched() {
 // the batch on two streams forked from the caller's stream (and joined back
 // before the call returns to it) lets one half's wave tails and short launches
 // overlap the other half's work.  The streams and events belong to the host
-// thread and device (created on first use); the fork / join pattern is also
+// thread and device: created on first use, destroyed when the thread exits
+// (a thread pool does not accumulate them); the fork / join pattern is also
 // valid inside a CUDA-graph capture of the caller's stream.
 constexpr int NSPLIT = 2;
 struct SplitStreams {
   cudaStream_t s[NSPLIT];
   cudaEvent_t fork, join[NSPLIT];
 };
+struct SplitStreamSets {
+  std::map<int, SplitStreams> by_device;
+  ~SplitStreamSets() {
+    // at thread exit; errors (a runtime already shut down at process exit)
+    // are ignored
+    for (auto& kv : by_device) {
+      for (int k = 0; k < NSPLIT; ++k) {
+        cudaStreamDestroy(kv.second.s[k]);
+        cudaEventDestroy(kv.second.join[k]);
+      }
+      cudaEventDestroy(kv.second.fork);
+    }
+  }
+};
 SplitStreams* split_streams() {
-  thread_local std::map<int, SplitStreams> sets;
+  thread_local SplitStreamSets holder;
+  std::map<int, SplitStreams>& sets = holder.by_device;
   int dev = 0;
   cudaGetDevice(&dev);
   auto it = sets.find(dev);

@@ -41,6 +41,7 @@
 //                      lower tiles.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -1544,6 +1545,152 @@ __global__ void __launch_bounds__(MC_THREADS) getrf_panel_mc_kernel(int n, int k
     }
     __syncthreads();
   }
+  for (int e = t; e < rc * kb; e += MC_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[(e / kb) * PS + (e % kb)];
+}
+
+// ------------------------------------------------------------------ cluster panel
+// The same factorization as getrf_panel_mc_kernel by one thread-block
+// cluster of G <= 16 CTAs per matrix (grid: G x batch, cluster G x 1): CTA c
+// keeps panel rows [c R, c R + R) in shared memory, and the candidates of a
+// pivot column are exchanged through distributed shared memory with one
+// hardware cluster barrier per column (release / acquire at cluster scope)
+// instead of a barrier and round trips through L2.  Candidates, candidate
+// rows and CTA 0's copy of row j are double-buffered by the parity of j (the
+// argument of getrf_panel_mc_kernel: a CTA overwrites buffer j mod 2 only
+// after the barrier of column j + 1, which every CTA passes after its reads
+// of column j).  Every CTA runs the same loop, so every barrier is reached by
+// the whole cluster; a first barrier makes the cluster's shared memory valid
+// before any remote access and a last one keeps every CTA resident until the
+// others' reads are done.  Pivots and arithmetic are those of the other
+// panel kernels (the candidates reduced in CTA order, the same scaling and
+// updates).
+constexpr int CL_MAX = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(MC_THREADS) getrf_panel_cl_kernel(int n, int k0, int kb, MatB<T> A, int* piv,
+                                                                     frob_info* info, int info_off, int R) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  using K = typename real_of<T>::type;
+  constexpr int PS = PANEL_MAX + 1;
+  const int b = blockIdx.y, t = threadIdx.x;
+  const int c = (int)cluster.block_rank(), G = (int)cluster.num_blocks();
+  const int m = n - k0;
+  const int row0 = c * R;
+  const int rc = max(0, min(R, m - row0));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);  // [R][PS]
+  __shared__ KeyIdx<K> red[MC_THREADS / 32];
+  __shared__ int redbad[MC_THREADS / 32];
+  __shared__ McKey<K> ckey[2];          // this CTA's candidate, by column parity
+  __shared__ T crow[2][PANEL_MAX];       // ... and its row
+  __shared__ T jrw[2][PANEL_MAX];        // CTA 0: row j before the exchange
+  __shared__ T pr[PANEL_MAX];            // the pivot row
+  __shared__ T jr[PANEL_MAX];            // row j, for the owner of the pivot row
+  __shared__ T s_rinv;
+  __shared__ int s_lwin, s_win, s_p, s_ok;
+  T* g = A.at(b) + (int64_t)(k0 + row0) * A.ld + k0;
+  for (int e = t; e < rc * kb; e += MC_THREADS) P[(e / kb) * PS + (e % kb)] = g[(int64_t)(e / kb) * A.ld + (e % kb)];
+  cluster.sync();
+  for (int j = 0; j < kb; ++j) {
+    const int par = j & 1;
+    KeyIdx<K> best{(K)-1, 0x7fffffff};
+    bool bad = false;
+    for (int lr = t; lr < rc; lr += MC_THREADS) {
+      const int gi = row0 + lr;
+      if (gi >= j) {
+        const K kv = pkey(P[lr * PS + j]);
+        if (!(kv == kv) || kv == (K)INFINITY) bad = true;
+        best = kmax(best, KeyIdx<K>{kv, gi});
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, best.key, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+      best = kmax(best, other);
+    }
+    const unsigned wbad = __ballot_sync(0xffffffffu, bad);
+    if ((t & 31) == 0) {
+      red[t >> 5] = best;
+      redbad[t >> 5] = wbad != 0;
+    }
+    __syncthreads();
+    if (t == 0) {
+      KeyIdx<K> bb = red[0];
+      int anybad = redbad[0];
+      for (int w = 1; w < MC_THREADS / 32; ++w) {
+        bb = kmax(bb, red[w]);
+        anybad |= redbad[w];
+      }
+      ckey[par].key = bb.key;
+      ckey[par].idx = bb.idx;
+      ckey[par].bad = anybad;
+      s_lwin = bb.idx;
+    }
+    __syncthreads();
+    if (t < kb) {
+      if (s_lwin != 0x7fffffff) crow[par][t] = P[(s_lwin - row0) * PS + t];
+      if (c == 0) jrw[par][t] = P[j * PS + t];
+    }
+    cluster.sync();  // publishes every CTA's candidate and CTA 0's row j
+    if (t < 32) {
+      KeyIdx<K> bb{(K)-1, 0x7fffffff};
+      int anybad = 0;
+      for (int q = t; q < G; q += 32) {
+        const McKey<K>* kq = cluster.map_shared_rank(&ckey[par], (unsigned)q);
+        anybad |= kq->bad;
+        bb = kmax(bb, KeyIdx<K>{kq->key, kq->idx});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        KeyIdx<K> other{__shfl_xor_sync(0xffffffffu, bb.key, o), __shfl_xor_sync(0xffffffffu, bb.idx, o)};
+        bb = kmax(bb, other);
+      }
+      anybad = __any_sync(0xffffffffu, anybad);
+      if (t == 0) {
+        const bool none = bb.idx == 0x7fffffff;
+        s_p = none ? j : bb.idx;
+        s_win = none ? -1 : bb.idx / R;
+        s_ok = !anybad && bb.key > (K)0;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (t < kb) {
+      pr[t] = s_win >= 0 ? cluster.map_shared_rank(&crow[par][0], (unsigned)s_win)[t] : P[j * PS + t];
+      if (p != j && p >= row0 && p < row0 + rc) jr[t] = cluster.map_shared_rank(&jrw[par][0], 0u)[t];
+    }
+    __syncthreads();
+    if (p != j && t < kb) {
+      if (p >= row0 && p < row0 + rc) P[(p - row0) * PS + t] = jr[t];
+      if (c == 0) P[j * PS + t] = pr[t];
+    }
+    if (t == 0) {
+      if (c == 0) {
+        piv[(int64_t)b * n + k0 + j] = k0 + p;
+        if (!s_ok) report(info, b, FROB_ERR_SINGULAR, info_off + k0 + j + 1);
+      }
+      s_rinv = s_ok ? recip_(pr[j]) : one_v<T>();
+    }
+    __syncthreads();
+    if (s_ok) {
+      const T rinv = s_rinv;
+      for (int lr = t; lr < rc; lr += MC_THREADS)
+        if (row0 + lr > j) P[lr * PS + j] = mul_(P[lr * PS + j], rinv);
+    }
+    __syncthreads();
+    {
+      constexpr int HALF = MC_THREADS / 2;
+      const int h = t / HALF;
+      for (int lr = t % HALF; lr < rc; lr += HALF) {
+        if (row0 + lr <= j) continue;
+        const T l = neg_(P[lr * PS + j]);
+        for (int cc = j + 1 + h; cc < kb; cc += 2) mac(P[lr * PS + cc], l, pr[cc]);
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // every remote read of this CTA's shared memory is done
   for (int e = t; e < rc * kb; e += MC_THREADS) g[(int64_t)(e / kb) * A.ld + (e % kb)] = P[(e / kb) * PS + (e % kb)];
 }
 

@@ -8,6 +8,9 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <type_traits>
 #include <cstdint>
@@ -456,6 +459,50 @@ inline int num_sms() {
   return sms > 0 ? sms : 1;
 }
 
+template <typename T> inline const char* getrf_cl_name() {
+  static const std::string s = std::string("getrf_panel_cl<") + type_tag<T>() + ">";
+  return s.c_str();
+}
+
+// Whether a cluster of G CTAs with `smem` bytes of dynamic shared memory each
+// can be scheduled for getrf_panel_cl_kernel<T> (asked once per shape and
+// device; cluster sizes above 8 need the non-portable opt-in).
+template <typename T> inline bool cluster_panel_ok(int G, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t>, bool> seen;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, G, smem);
+  auto it = seen.find(key);
+  if (it != seen.end()) return it->second;
+  // the largest size any shape uses, so that a later launch of a cached
+  // shape is never refused for a smaller limit set in between
+  bool ok = cudaFuncSetAttribute(getrf_panel_cl_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MC_SMEM_MAX) == cudaSuccess;
+  if (ok && G > 8)
+    ok = cudaFuncSetAttribute(getrf_panel_cl_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+         cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G, 1, 1);
+    cfg.blockDim = dim3(MC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    ok = cudaOccupancyMaxActiveClusters(&clusters, getrf_panel_cl_kernel<T>, &cfg) == cudaSuccess && clusters >= 1;
+  }
+  cudaGetLastError();  // a refused attribute or query leaves no error behind
+  seen[key] = ok;
+  return ok;
+}
+
 template <typename T> inline const char* getrf_mc_name() {
   static const std::string s = std::string("getrf_panel_mc<") + type_tag<T>() + ">";
   return s.c_str();
@@ -476,12 +523,48 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
     const size_t bytes = (size_t)m * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
     int R = 0, G = 0;
-    if (mc && m > PANEL_THREADS) {
+    // a thread-block cluster holding the whole panel (exchange through
+    // distributed shared memory), when its rows fit 16 CTAs' shared memory
+    int Rc = 0, Gc = 0;
+    if (mc && m > PANEL_THREADS && batch * CL_MAX <= num_sms()) {
+      Gc = std::min(CL_MAX, (m + MC_MIN_ROWS - 1) / MC_MIN_ROWS);
+      Rc = (m + Gc - 1) / Gc;
+      const size_t smem_c = (size_t)Rc * (PANEL_MAX + 1) * sizeof(T);
+      if (smem_c > MC_SMEM_MAX || !cluster_panel_ok<T>(Gc, smem_c)) Gc = 0;
+    }
+    if (Gc == 0 && mc && m > PANEL_THREADS) {
       R = std::max(MC_MIN_ROWS, (m + gcap - 1) / gcap);
       G = (m + R - 1) / R;
       if (mc_smem<T>(R) > MC_SMEM_MAX) G = 0;
     }
-    if (G > 0) {
+    if (Gc > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)Gc, (unsigned)batch, 1);
+      cfg.blockDim = dim3(MC_THREADS, 1, 1);
+      cfg.dynamicSmemBytes = (size_t)Rc * (PANEL_MAX + 1) * sizeof(T);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)Gc;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaError_t le = cudaSuccess;
+      FROB_LAUNCH(getrf_cl_name<T>(), st,
+                  le = cudaLaunchKernelEx(&cfg, getrf_panel_cl_kernel<T>, n, k0, kb, A, piv, info, info_off, Rc));
+      if (le != cudaSuccess) {
+        // refused (e.g. no room for the cluster): the cooperative-grid panel
+        cudaGetLastError();
+        R = std::max(MC_MIN_ROWS, (m + gcap - 1) / gcap);
+        G = (m + R - 1) / R;
+        if (mc_smem<T>(R) > MC_SMEM_MAX) G = 0;
+        Gc = 0;
+      }
+    }
+    if (Gc > 0) {
+      // launched on the cluster
+    } else if (G > 0) {
       const size_t smem = mc_smem<T>(R);
       int64_t bs = (int64_t)mc_scratch_per_matrix<T>();
       long long limit = 1ll << 31;  // about a second of SM clock

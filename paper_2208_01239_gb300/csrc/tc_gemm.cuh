@@ -19,7 +19,10 @@
 //
 // Every wait on an mbarrier is bounded by the global timer: a wait that runs
 // out sets an error flag (the caller's `err` word) and the thread stops
-// waiting; the CTA still releases its TMEM and returns.
+// waiting; before the CTA releases its TMEM and returns, the producer waits
+// (bounded again) for the copies it issued that were not consumed.  The flag
+// is best-effort: after FROB_ERR_TIMEOUT the results are unusable and the
+// context should be treated as suspect.
 #pragma once
 
 #include <cstdint>

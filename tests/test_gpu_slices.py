@@ -93,3 +93,32 @@ def test_autotuned_split_gives_the_same_results(F):
     finally:
         F.autotune(False)
         F.autotune_clear()
+
+
+def test_calls_from_short_lived_threads(F):
+    """Each host thread's split streams are destroyed when it exits: batched
+    calls from several short-lived threads, one after another and then
+    concurrently, give the results of the calling thread."""
+    import threading
+    ms = W.gaussian(48, 2, seed=61)
+    ref = F.frob_inv(torch.from_numpy(ms).cuda()).x.cpu().numpy()
+    out = {}
+
+    def work(k):
+        torch.cuda.set_device(0)
+        x = F.frob_inv(torch.from_numpy(ms).cuda()).x
+        torch.cuda.synchronize()
+        out[k] = x.cpu().numpy()
+
+    for k in range(3):
+        t = threading.Thread(target=work, args=(k,))
+        t.start()
+        t.join()
+    ts = [threading.Thread(target=work, args=(10 + k,)) for k in range(3)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert sorted(out) == [0, 1, 2, 10, 11, 12]
+    for v in out.values():
+        assert np.array_equal(v, ref)
