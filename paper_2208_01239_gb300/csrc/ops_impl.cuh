@@ -403,6 +403,22 @@ inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cu
       // with the FP64 digit products on: each pair as two full products on
       // the tensor cores (the zero triangles included), one pair per launch
       if (t_oz.p && s >= ozr::MIN_MNK && sc >= ozr::MIN_MNK) {
+        if (batch == 1 && npairs > 1) {
+          // the pairs of this level are equal blocks spaced 2 s down the
+          // diagonal: one batched product each, batch stride 2 s (ld + 1)
+          auto step = [&](auto m) {
+            auto v = m;
+            v.bs = 2 * (int64_t)s * (m.ld + 1);
+            return v;
+          };
+          MatB<T> Tq = step(Tmp.sub(r + s, r));
+          gemm_launch<T, OP_N, OP_N>(sc, s, s, npairs, step(Lm.sub(r + s, r)), step(cst(X.sub(r, r))),
+                                     axpby<T>(Tq, one_v<T>(), zero_v<T>(), true), 0, st);     // B A^{-1}
+          gemm_launch<T, OP_N, OP_N>(sc, s, sc, npairs, step(cst(X.sub(r + s, r + s))), cst(Tq),
+                                     axpby<T>(step(X.sub(r + s, r)), neg_(one_v<T>()), zero_v<T>(), true), 0,
+                                     st);                                                       // -C^{-1} (B A^{-1})
+          return;
+        }
         for (int q = 0; q < npairs; ++q) {
           const int rq = r + 2 * s * q;
           MatB<T> Tq = Tmp.sub(rq + s, rq);
