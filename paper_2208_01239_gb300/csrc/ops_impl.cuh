@@ -1042,6 +1042,8 @@ template <typename R> struct SolvePlanes {
   MatB<R> LA, S, Bp, X1, CD, T, U;
   int *piv1, *piv2, *rp1, *rp2;
   unsigned char* mcs;
+  unsigned char* tcs;  // tensor-core products' scratch (split TF32 / FP64 digits)
+  size_t tcs_bytes;
 };
 
 template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlanes<R>* out, void* ws) {
@@ -1063,6 +1065,8 @@ template <typename R> size_t frob_solve_ws(int n, int nrhs, int batch, SolvePlan
   p.rp1 = c.take<int>((size_t)n * batch);
   p.rp2 = c.take<int>((size_t)n * batch);
   p.mcs = c.take<unsigned char>(mc_scratch_bytes<R>(n, batch));
+  p.tcs_bytes = std::is_same<R, float>::value ? tc_scratch_for(n, batch) : oz_scratch_for(n, batch);
+  p.tcs = c.take<unsigned char>(p.tcs_bytes);
   if (out) *out = p;
   return c.off;
 }
@@ -1073,6 +1077,9 @@ void frob_solve_run(int n, int nrhs, int batch, MatB<const typename cplx_of<R>::
                     frob_info* info, cudaStream_t st) {
   SolvePlanes<R> p;
   frob_solve_ws<R>(n, nrhs, batch, &p, ws);
+  // the large products (S = A + B X1, the B [y1 | x1] products) on the tensor cores
+  TcScope tc_scope(p.tcs, p.tcs_bytes, info, batch, st, std::is_same<R, float>::value);
+  OzScope oz_scope(p.tcs, p.tcs_bytes, info, batch, st, std::is_same<R, double>::value);
   auto cst = [](MatB<R> m) { return MatB<const R>{m.p, m.ld, m.bs}; };
   const int m2 = 2 * nrhs;
   FROB_LAUNCH("split", st, split_kernel<R><<<elem_grid(n, batch), 256, 0, st>>>(n, M, p.LA, p.S, p.Bp, info, 0, 0, 0, 0));
