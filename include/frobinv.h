@@ -259,6 +259,30 @@ frob_status frob_gemm_tc(int kind, int M, int N, int K, int batch, const float* 
 size_t frob_gemm_tc_workspace_bytes(int kind, int M, int N, int K, int batch);
 
 /*
+ * frob_gemm_f64 -- the FP64 digit-product GEMM building block (no
+ * counterpart in the paper; it carries Frobenius inversion's FP64 products,
+ * see frob_opts.fp64_gemm): C[b] = alpha op(A[b]) op(B[b]) + beta C[b] with
+ * op(A) M x K, op(B) K x N, row-major FP64 on the device (op(A) = A^T when
+ * transA = 1, likewise B), as exact BF16 digit products on the tensor cores:
+ * each row of op(A) and column of op(B) scaled by a power of two and written
+ * with eight signed 7-bit digits, the 36 digit pairs of weight 2^-14 ..
+ * 2^-63 multiplied with FP32 accumulation (exact per 512-wide K chunk) and
+ * summed exactly in 64-bit fixed point.  The error is at most about 2^-57
+ * sqrt(K) of the row and column maxima, below an FP64 product's.  A row or
+ * column holding an infinity or a NaN gives NaN entries.  beta = 0: C is not
+ * read.  M and N are at least 128 and K at least 1 (FROB_ERR_ARG
+ * otherwise; K <= 128 is padded to 128, so a thin product costs as much as
+ * one of K = 128), batch at most 65535.  `err` is a device int set to FROB_ERR_TIMEOUT if a bounded wait
+ * gave up (the caller zeroes it).  Workspace:
+ * frob_gemm_f64_workspace_bytes(M, N, K, batch) bytes (0 for invalid sizes),
+ * 256-aligned; about 16 (M + N) K batch bytes.
+ */
+frob_status frob_gemm_f64(int M, int N, int K, int batch, const double* A, int64_t lda, int64_t sa, int transA,
+                          const double* B, int64_t ldb, int64_t sb, int transB, double* C, int64_t ldc, int64_t sc,
+                          double alpha, double beta, void* ws, size_t wsb, int* err, void* stream);
+size_t frob_gemm_f64_workspace_bytes(int M, int N, int K, int batch);
+
+/*
  * frob_inv_adjoint -- reverse-mode derivative of inversion: for X = M^{-1}
  * and the gradient G of a real loss with respect to X (G = dL/dRe X +
  * i dL/dIm X, PyTorch's convention), writes gradM = -X^H G X^H, which follows

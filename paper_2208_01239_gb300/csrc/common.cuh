@@ -14,6 +14,7 @@
 #include <mutex>
 #include <set>
 #include <tuple>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "../../include/frobinv.h"
@@ -182,6 +183,24 @@ inline bool smem_attr_needed(const void* fn, int bytes) {
 template <typename F> inline void set_smem_attr(F* kernel, int bytes) {
   if (smem_attr_needed(reinterpret_cast<const void*>(kernel), bytes))
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Element-wise GEMM epilogues applied to W consecutive columns j0 .. j0 + W - 1
+// of row i (those below ncols): a functor with a row<W>() method (kRow) reads
+// every input of the W elements before it writes any, so that the loads are
+// in flight together; other functors are called element by element.
+template <class E, class = void> struct epi_has_row : std::false_type {};
+template <class E> struct epi_has_row<E, std::void_t<decltype(E::kRow)>> : std::true_type {};
+
+template <int W, class Epi, typename T>
+__device__ __forceinline__ void epi_row(const Epi& epi, int b, int i, int j0, const T (&v)[W], int ncols) {
+  if constexpr (epi_has_row<Epi>::value) {
+    epi.template row<W>(b, i, j0, v, ncols);
+  } else {
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (j0 + q < ncols) epi(b, i, j0 + q, v[q]);
+  }
 }
 
 #define FROB_LAUNCH(NAME, ST, ...)    \

@@ -168,6 +168,24 @@ template <typename T> struct EpiAxpby {
     if (!beta_is_zero) out = add_(out, mul_(beta, C.at(b)[(int64_t)i * C.ld + j]));
     D.at(b)[(int64_t)i * D.ld + j] = out;
   }
+  static constexpr bool kRow = true;
+  template <int W>
+  __device__ __forceinline__ void row(int b, int i, int j0, const T (&v)[W], int ncols) const {
+    T* d = D.at(b) + (int64_t)i * D.ld + j0;
+    if (!beta_is_zero) {
+      const T* c = C.at(b) + (int64_t)i * C.ld + j0;
+      T cv[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) cv[q] = (j0 + q < ncols) ? c[q] : zero_v<T>();
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+        if (j0 + q < ncols) d[q] = add_(mul_(alpha, v[q]), mul_(beta, cv[q]));
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+        if (j0 + q < ncols) d[q] = mul_(alpha, v[q]);
+    }
+  }
 };
 
 // The last product of Frobenius inversion, W = X1 Z with Z = S^{-1} (up to
@@ -206,6 +224,39 @@ template <typename R> struct EpiFrobOut {
       out.y = x4;
     }
     X.at(b)[(int64_t)i * X.ld + jd] = out;
+  }
+  static constexpr bool kRow = true;
+  template <int W>
+  __device__ __forceinline__ void row(int b, int i, int j0, const R (&w)[W], int ncols) const {
+    const R* z = Z.at(b) + (int64_t)i * Z.ld + j0;
+    R x3[W];
+    int jd[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const bool in = j0 + q < ncols;
+      x3[q] = in ? z[q] : R(0);
+      jd[q] = (in && rp) ? rp[(int64_t)b * n + j0 + q] : j0 + q;
+    }
+    const R mu = info ? (R)info[b].mu : R(0);
+    const bool swap = !info && partb && partb[b];
+    C* x = X.at(b) + (int64_t)i * X.ld;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      if (j0 + q >= ncols) continue;
+      const R x4 = -w[q];
+      C out;
+      if (info) {
+        out.x = x3[q] - mu * x4;
+        out.y = mu * x3[q] + x4;
+      } else if (swap) {
+        out.x = x4;
+        out.y = -x3[q];
+      } else {
+        out.x = x3[q];
+        out.y = x4;
+      }
+      x[jd[q]] = out;
+    }
   }
 };
 

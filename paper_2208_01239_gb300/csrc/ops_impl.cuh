@@ -256,7 +256,7 @@ inline void gemm_launch(int M, int N, int K, int batch, MatB<const T> A, MatB<co
     }
   }
   if constexpr (std::is_same<T, double>::value) {
-    if (tile_mode == 0 && npairs == 1 && t_oz.p && M >= ozr::MIN_MNK && N >= ozr::MIN_MNK && K >= ozr::MIN_MNK &&
+    if (tile_mode == 0 && npairs == 1 && t_oz.p && ozr::digit_shape(M, N, K) &&
         ozr::scratch_bytes(M, N, K, batch) <= t_oz.bytes) {
       CUtensorMap ma, mb;
       ozr::RArgs ra;

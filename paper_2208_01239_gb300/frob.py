@@ -121,6 +121,11 @@ def load() -> ctypes.CDLL:
         lib.frob_gemm_tc.restype = i32
         lib.frob_gemm_tc_workspace_bytes.argtypes = [i32, i32, i32, i32, i32]
         lib.frob_gemm_tc_workspace_bytes.restype = sz
+        lib.frob_gemm_f64.argtypes = [i32, i32, i32, i32, vp, i64, i64, i32, vp, i64, i64, i32, vp, i64, i64,
+                                      ctypes.c_double, ctypes.c_double, vp, sz, vp, vp]
+        lib.frob_gemm_f64.restype = i32
+        lib.frob_gemm_f64_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        lib.frob_gemm_f64_workspace_bytes.restype = sz
         lib.frob_newton_workspace_bytes.argtypes = [i32, i32, i32, i32]
         lib.frob_newton_workspace_bytes.restype = sz
         lib.frob_polar_workspace_bytes.argtypes = [i32, i32, i32, i32]
@@ -684,6 +689,59 @@ def gemm_tc(a: torch.Tensor, b: torch.Tensor, kind: str = "bf16", out: torch.Ten
     if e != 0:
         raise FrobError(f"gemm_tc: device status {status_str(e)}", e)
     return c3 if (a.dim() == 3 or out is not None) else c3[0]
+
+
+def gemm_f64(a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: bool = False,
+             alpha: float = 1.0, beta: float = 0.0, out: torch.Tensor | None = None,
+             ws: torch.Tensor | None = None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C in FP64 as exact BF16 digit products on
+    the tensor cores: A (batch, M, K) (or (batch, K, M) with trans_a), B
+    (batch, K, N) (or (batch, N, K) with trans_b), FP64 on the GPU, M and
+    N >= 128.  Returns C (batch, M, N) FP64 (the `out` tensor when given)."""
+    lib = load()
+    a3 = a if a.dim() == 3 else a.unsqueeze(0)
+    b3 = b if b.dim() == 3 else b.unsqueeze(0)
+    if a3.dtype != torch.float64 or b3.dtype != torch.float64 or not a3.is_cuda:
+        raise TypeError("gemm_f64: FP64 CUDA tensors expected")
+    if a3.stride(-1) != 1:
+        a3 = a3.contiguous()
+    if b3.stride(-1) != 1:
+        b3 = b3.contiguous()
+    batch = a3.shape[0]
+    M, K = (a3.shape[2], a3.shape[1]) if trans_a else (a3.shape[1], a3.shape[2])
+    N = b3.shape[1] if trans_b else b3.shape[2]
+    if (b3.shape[2] if trans_b else b3.shape[1]) != K or b3.shape[0] != batch:
+        raise ValueError("gemm_f64: inner dimensions or batch differ")
+    if out is None:
+        c3 = torch.empty((batch, M, N), dtype=torch.float64, device=a3.device)
+        beta = 0.0
+    else:
+        c3 = out if out.dim() == 3 else out.unsqueeze(0)
+        if c3.stride(-1) != 1 or tuple(c3.shape) != (batch, M, N) or c3.dtype != torch.float64:
+            raise ValueError("gemm_f64: out must be a row-major FP64 (batch, M, N) tensor")
+    need = int(lib.frob_gemm_f64_workspace_bytes(M, N, K, batch))
+    if need == 0:
+        raise ValueError("gemm_f64: M and N must be at least 128")
+    if ws is None:
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=a3.device)
+    pad = (-ws.data_ptr()) % 256
+    err = torch.zeros(1, dtype=torch.int32, device=a3.device)
+    def ld(t):  # a single row's stride is arbitrary (NumPy, torch): any value >= its length serves
+        return t.stride(1) if t.shape[1] > 1 else t.shape[2]
+
+    bs_c = c3.stride(0) if batch > 1 else M * ld(c3)
+    st = lib.frob_gemm_f64(M, N, K, batch, a3.data_ptr(), ld(a3), a3.stride(0), int(trans_a),
+                           b3.data_ptr(), ld(b3), b3.stride(0), int(trans_b), c3.data_ptr(), ld(c3),
+                           bs_c, float(alpha), float(beta), ws.data_ptr() + pad, ws.numel() - pad, err.data_ptr(),
+                           torch.cuda.current_stream(a3.device).cuda_stream)
+    if st != FROB_OK:
+        raise FrobError(f"gemm_f64: {status_str(st)}", st)
+    e = int(err.item())
+    if e != 0:
+        raise FrobError(f"gemm_f64: device status {status_str(e)}", e)
+    if out is not None:
+        return out
+    return c3 if a.dim() == 3 else c3[0]
 
 
 def draw_mu(seed: int, b: int, attempt: int = 0) -> float:
