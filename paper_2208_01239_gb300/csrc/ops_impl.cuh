@@ -327,20 +327,90 @@ __global__ void rowgather_kernel(int n, int ncols, MatB<const T> B, MatB<T> X, c
   X.at(b)[(int64_t)r * X.ld + c] = B.at(b)[(int64_t)sr * B.ld + c];
 }
 
+template <typename T>
+__global__ void copy2d_kernel(int rows, int cols, MatB<const T> S, MatB<T> D) {
+  const int b = blockIdx.z;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  D.at(b)[(int64_t)r * D.ld + c] = S.at(b)[(int64_t)r * S.ld + c];
+}
+
+template <typename T, bool UNIT>
+inline void trtri(int n, int batch, MatB<const T> Lm, MatB<T> X, MatB<T> Tmp, cudaStream_t st);
+
+// Explicit inverses of the diagonal blocks of a recursive triangular solve
+// (all blocks of at most TRSM_REC_BASE rows, padded to TRSM_REC_BASE with the
+// identity): inverse q of matrix b at G + (q batch + b) RB^2, row-major with
+// ld RB.  `off[q]` is block q's first row.
+constexpr int REC_INV_MAX = 64;
+struct RecInv {
+  const double* G;
+  int nb;
+  int off[REC_INV_MAX];
+};
+
+struct RecBlocks {
+  int nb;
+  int off[REC_INV_MAX];
+  int sz[REC_INV_MAX];
+};
+
+// Padded copies of the diagonal blocks: D[q][b] = [B 0; 0 I] with B the
+// block of T (transposed when `trans`), grid (RB^2 / 256, nb, batch).
+template <int RB>
+__global__ void gather_diag_kernel(RecBlocks blk, int trans, MatB<const double> Tm, double* D, int batch) {
+  const int q = blockIdx.y, b = blockIdx.z;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= RB * RB) return;
+  const int r = e / RB, c = e % RB;
+  const int o = blk.off[q], sz = blk.sz[q];
+  double v = r == c ? 1.0 : 0.0;
+  if (r < sz && c < sz) {
+    const double* Tb = Tm.at(b);
+    v = trans ? Tb[(int64_t)(o + c) * Tm.ld + (o + r)] : Tb[(int64_t)(o + r) * Tm.ld + (o + c)];
+  }
+  D[((int64_t)q * batch + b) * RB * RB + e] = v;
+}
+
 // Recursive triangular solve op(T) X = X in place (Elmroth, Gustavson,
 // Jonsson and Kagstrom's recursive blocking): split at h, solve the first
 // half, remove its contribution from the second half with one product,
 // solve the second half.  Almost all of the n^2 nrhs flops land in large
 // products that spread over the whole GPU, where the block-row steps of
 // trsm() have only ceil(nrhs / 64) x batch CTAs each; blocks of at most
-// TRSM_REC_BASE rows use trsm().
+// TRSM_REC_BASE rows are one digit product with their explicit inverse
+// (computed for all blocks at once by rec_inverses) when the FP64 digit
+// products are on, else trsm().
 constexpr int TRSM_REC_BASE = 256;
 constexpr int TRSM_REC_MIN = 1024;   // smallest order that takes the recursive form
 constexpr int TRSM_REC_TILES = 512;  // ... when ceil(nrhs / 64) x batch is at most this
 
 template <typename T, int OPT, bool LOWER, bool UNIT>
-inline void trsm_rec(int n, int nrhs, int batch, MatB<const T> Tm, MatB<T> X, cudaStream_t st) {
+inline void trsm_rec(int n, int nrhs, int batch, MatB<const T> Tm, MatB<T> X, cudaStream_t st,
+                     const RecInv* inv = nullptr, int r0 = 0) {
   if (n <= TRSM_REC_BASE) {
+    if constexpr (std::is_same<T, double>::value) {
+      if (inv) {
+        // X = G X with G = op(T)^{-1} (LOWER) or its transpose (upper op(T)),
+        // formed out of place behind the inverses, then copied back
+        int q = 0;
+        while (q < inv->nb && inv->off[q] != r0) ++q;
+        const int64_t rr = (int64_t)TRSM_REC_BASE * TRSM_REC_BASE;
+        MatB<const double> Gq{inv->G + (int64_t)q * batch * rr, TRSM_REC_BASE, rr};
+        MatB<double> Y{const_cast<double*>(inv->G) + (int64_t)inv->nb * batch * rr, nrhs, (int64_t)n * nrhs};
+        MatB<const double> Xc{X.p, X.ld, X.bs};
+        if (LOWER)
+          gemm_launch<double, OP_N, OP_N>(n, nrhs, n, batch, Gq, Xc, axpby<double>(Y, 1.0, 0.0, true), 0, st);
+        else
+          gemm_launch<double, OP_T, OP_N>(n, nrhs, n, batch, Gq, Xc, axpby<double>(Y, 1.0, 0.0, true), 0, st);
+        const int64_t ne = (int64_t)n * nrhs;
+        FROB_LAUNCH("copy2d", st,
+                    copy2d_kernel<double><<<dim3((unsigned)((ne + 255) / 256), 1, (unsigned)batch), 256, 0, st>>>(
+                        n, nrhs, MatB<const double>{Y.p, Y.ld, Y.bs}, X));
+        return;
+      }
+    }
     trsm<T, OPT, LOWER, UNIT, false>(n, nrhs, batch, Tm, MatB<const T>{X.p, X.ld, X.bs}, X, nullptr, st);
     return;
   }
@@ -349,15 +419,71 @@ inline void trsm_rec(int n, int nrhs, int batch, MatB<const T> Tm, MatB<T> X, cu
   auto blk = [&](int i0, int j0) { return OPT == OP_N ? Tm.sub(i0, j0) : Tm.sub(j0, i0); };
   auto cst = [](MatB<T> m) { return MatB<const T>{m.p, m.ld, m.bs}; };
   if (LOWER) {
-    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st);
+    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st, inv, r0);
     gemm_launch<T, OPT, OP_N>(n - h, nrhs, h, batch, blk(h, 0), cst(X), axpby<T>(X.sub(h, 0), neg_(one_v<T>()),
                                                                                  one_v<T>(), false), 0, st);
-    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st);
+    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st, inv, r0 + h);
   } else {
-    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st);
+    trsm_rec<T, OPT, LOWER, UNIT>(n - h, nrhs, batch, Tm.sub(h, h), X.sub(h, 0), st, inv, r0 + h);
     gemm_launch<T, OPT, OP_N>(h, nrhs, n - h, batch, blk(0, h), cst(X.sub(h, 0)),
                               axpby<T>(X, neg_(one_v<T>()), one_v<T>(), false), 0, st);
-    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st);
+    trsm_rec<T, OPT, LOWER, UNIT>(h, nrhs, batch, Tm, X, st, inv, r0);
+  }
+}
+
+// The diagonal blocks trsm_rec reaches for order n (first row, rows).
+inline void rec_blocks(int n, int r0, RecBlocks& out) {
+  if (n <= TRSM_REC_BASE) {
+    if (out.nb < REC_INV_MAX) {
+      out.off[out.nb] = r0;
+      out.sz[out.nb] = n;
+    }
+    ++out.nb;
+    return;
+  }
+  const int h = ((n / 2 + TB - 1) / TB) * TB;
+  rec_blocks(h, r0, out);
+  rec_blocks(n - h, r0 + h, out);
+}
+
+// With the FP64 digit products on: the inverses of all diagonal blocks of
+// the recursion in one batched triangular inverse, at the end of the digit
+// scratch (behind the largest product's digits), so that each block of the
+// solve is one digit product.  False (nothing done) when the blocks are too
+// many or the scratch is short.
+template <typename T, int OPT, bool LOWER, bool UNIT>
+inline bool rec_inverses(int n, int nrhs, int batch, MatB<const T> Tm, RecInv& inv, cudaStream_t st) {
+  if constexpr (!std::is_same<T, double>::value) {
+    return false;
+  } else {
+    if (!t_oz.p || nrhs < ozr::MIN_MN_THIN) return false;
+    RecBlocks blk{};
+    rec_blocks(n, 0, blk);
+    if (blk.nb > REC_INV_MAX) return false;
+    for (int q = 0; q < blk.nb; ++q)
+      if (!ozr::digit_shape(blk.sz[q], nrhs, blk.sz[q])) return false;
+    constexpr int RB = TRSM_REC_BASE;
+    const size_t plane = (size_t)blk.nb * batch * RB * RB * sizeof(double);
+    const size_t ybytes = (size_t)RB * nrhs * batch * sizeof(double);
+    const size_t tail = (3 * plane + ybytes + 511) & ~(size_t)255;
+    const int h = ((n / 2 + TB - 1) / TB) * TB;
+    const size_t head = std::max(ozr::scratch_bytes(n - h, nrhs, h, batch), ozr::scratch_bytes(RB, nrhs, RB, batch));
+    if (head + 256 + tail > t_oz.bytes) return false;
+    // [G: inverses][Y: products of one block][D: padded blocks][J: join scratch]
+    double* G = reinterpret_cast<double*>(t_oz.p + ((t_oz.bytes - tail) & ~(size_t)255));
+    double* D = G + plane / sizeof(double) + ybytes / sizeof(double);
+    double* J = D + plane / sizeof(double);
+    constexpr bool transpose = (LOWER && OPT != OP_N) || (!LOWER && OPT == OP_N);
+    FROB_LAUNCH("gather_diag", st,
+                (gather_diag_kernel<RB><<<dim3(RB * RB / 256, (unsigned)blk.nb, (unsigned)batch), 256, 0, st>>>(
+                    blk, transpose ? 1 : 0, Tm, D, batch)));
+    const int64_t rr = (int64_t)RB * RB;
+    trtri<double, UNIT>(RB, blk.nb * batch, MatB<const double>{D, RB, rr}, MatB<double>{G, RB, rr},
+                        MatB<double>{J, RB, rr}, st);
+    inv.G = G;
+    inv.nb = blk.nb;
+    for (int q = 0; q < blk.nb; ++q) inv.off[q] = blk.off[q];
+    return true;
   }
 }
 
@@ -378,7 +504,9 @@ inline void trsm_any(int n, int nrhs, int batch, MatB<const T> Tm, MatB<const T>
                 rowgather_kernel<T><<<dim3((unsigned)((ne + 255) / 256), 1, (unsigned)batch), 256, 0, st>>>(
                     n, nrhs, Bm, X, rowperm));
   }
-  trsm_rec<T, OPT, LOWER, UNIT>(n, nrhs, batch, Tm, X, st);
+  RecInv inv;
+  const bool have_inv = rec_inverses<T, OPT, LOWER, UNIT>(n, nrhs, batch, Tm, inv, st);
+  trsm_rec<T, OPT, LOWER, UNIT>(n, nrhs, batch, Tm, X, st, have_inv ? &inv : nullptr, 0);
 }
 
 // X = L^{-1} for lower triangular L (unit diagonal if UNIT), recursively:
@@ -630,15 +758,6 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
 // inverse (w1 x w1) and its join scratch (w1 x w1, beside it) fit in tmp.
 constexpr int GETRF_REC_NB = 2048;
 constexpr int GETRF_REC_NB_INV = 512;
-
-template <typename T>
-__global__ void copy2d_kernel(int rows, int cols, MatB<const T> S, MatB<T> D) {
-  const int b = blockIdx.z;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)rows * cols) return;
-  const int r = (int)(e / cols), c = (int)(e % cols);
-  D.at(b)[(int64_t)r * D.ld + c] = S.at(b)[(int64_t)r * S.ld + c];
-}
 
 template <typename T>
 inline void getrf_rec(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,

@@ -66,12 +66,15 @@ namespace ozr {
 // against FP64 in the cancelling updates of triangular solves)
 constexpr int S_DIG = 8;
 constexpr int KC = 512;           // K per exact chunk
-constexpr int MIN_MNK = 256;      // products smaller than this in any dimension stay on the CUDA cores ...
-// ... unless thin: K <= SMALL_KP (one 128-wide sub-chunk, split in one pass
-// by ozr_digits_small_kernel), M and N >= MIN_MN_THIN and M N >= THIN_MIN_MN
-// (the rank-32 updates of LU panels, about 0.6 TFLOP/s on the FP64 pipe)
+constexpr int MIN_MNK = 256;      // products at least this large in every dimension take the digit path ...
+// ... and so do smaller ones with M, N >= MIN_MN_THIN and M N K >= THIN_MIN_MNK
+// (the rank-32 updates of LU panels and the diagonal blocks of the recursive
+// triangular solves): a digit product costs about 70 us plus 14 us per 10^6
+// M N and 128-wide K slice, the FP64 pipe about 105 us per 10^6 M N and 32 K
+constexpr int MIN_MN_THIN = 128;
+constexpr int64_t THIN_MIN_MNK = 24ll << 20;
 constexpr int SUB = KC / (oz::KB * oz::CHUNK_KB);  // 128-wide sub-chunks per chunk (4)
-constexpr int SMALL_KP = 128;
+constexpr int SMALL_KP = 128;     // K up to this: split in one pass (ozr_digits_small_kernel)
 // shared memory of ozr_gemm_kernel: four resident A chunks (two digits in use,
 // two loading) and three B stages of 32 KB each
 constexpr int R_A_BUFS = 4;
@@ -81,8 +84,6 @@ constexpr int R_SMEM_BYTES = (R_A_BUFS + R_B_STAGES) * oz::A_CHUNK_BYTES + 1024 
 static_assert(oz::A_CHUNK_BYTES == oz::B_STAGE_BYTES, "A chunks and B stages of one size");
 static_assert(R_SMEM_BYTES <= 232448, "shared memory per CTA");
 constexpr int EPI_W = 4;          // output columns per epilogue block
-constexpr int MIN_MN_THIN = 128;
-constexpr int64_t THIN_MIN_MN = 131072;
 // exponent of a row / column that holds an infinity or a NaN: its digits are
 // zero and every product entry it touches is NaN, as on the CUDA cores
 constexpr int NONFINITE_EXP = 0x40000000;
@@ -561,7 +562,7 @@ size_t scratch_bytes(int M, int N, int K, int batch);
 // whether a product of this shape takes the digit path (when scratch allows)
 inline bool digit_shape(int M, int N, int K) {
   if (M >= MIN_MNK && N >= MIN_MNK && K >= MIN_MNK) return true;
-  return K >= 1 && K <= SMALL_KP && M >= MIN_MN_THIN && N >= MIN_MN_THIN && (int64_t)M * N >= THIN_MIN_MN;
+  return K >= 1 && M >= MIN_MN_THIN && N >= MIN_MN_THIN && (int64_t)M * N * K >= THIN_MIN_MNK;
 }
 // Splits op(A) (M x K: A[i][k], or A[k][i] with transA) and op(B) (its
 // columns: B[k][j], or B[j][k] with transB_rows -- op(B)^T's rows stored

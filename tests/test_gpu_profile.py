@@ -41,11 +41,16 @@ def test_profile_flops_match_executed_count(F, op, alg, n):
     # as full products on the tensor cores (at most n^3 / 3 more), and, above
     # order 512, the recursive LU's U12 = (L11^{-1}) A12 in place of a solve
     # (per block split, 2 w1^3 / 3 for the inverse and w1^2 (w - w1) more for
-    # the product: at most about n^3 / 6 over both factorizations)
+    # the product: at most about n^3 / 6 over both factorizations), and, from
+    # order 1024 on, the recursive triangular solves' diagonal blocks of up to
+    # 256 rows as full products with the blocks' inverses (256^2 nrhs more per
+    # block of 256 rows, 256 n^2 per solve, three solves)
     hi = 1.03
     if alg == "frob_lu" and n >= 256:
         hi += (1 / 3) / float(flops.EXECUTED[alg])
     if alg == "frob_lu" and n > 512:
         hi += (1 / 6) / float(flops.EXECUTED[alg])
+    if alg == "frob_lu" and n >= 1024:
+        hi += 3 * 256 / n / float(flops.EXECUTED[alg])
     assert 0.90 * want <= counted <= hi * want, (counted / want, rep)
     assert all(v[1] > 0 for v in rep.values())
