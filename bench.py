@@ -729,8 +729,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload, its complex-LU baseline and the end-to-end number")
-    ap.add_argument("--once", default=None, choices=["frob_inv", "cplx_lu_inv", "frob_inv_hpd", "frob_inv_hpd_mixed"],
-                    help="run one inversion of the workload twice and exit: the command profiled by ncu")
+    ap.add_argument("--once", default=None,
+                    choices=["frob_inv", "cplx_lu_inv", "frob_inv_hpd", "frob_inv_hpd_mixed", "gemm_f64"],
+                    help="run one inversion of the workload (gemm_f64: one n x n x n FP64 digit product, "
+                         "C = C - A B) twice and exit: the command profiled by ncu")
     ap.add_argument("--n", type=int, default=N_ORDER, help="order for --once (profiling a smaller case)")
     ap.add_argument("--batch", type=int, default=64, help="matrices for --once frob_inv_hpd_mixed")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision for --once")
@@ -762,6 +764,16 @@ def main():
     sync = lambda: torch.cuda.synchronize(dev)
 
     if args.once:
+        if args.once == "gemm_f64":
+            g = torch.Generator(device="cpu").manual_seed(SEED)
+            a = torch.randn(args.n, args.n, dtype=torch.float64, generator=g).to(dev)
+            b = torch.randn(args.n, args.n, dtype=torch.float64, generator=g).to(dev)
+            c = torch.randn(args.n, args.n, dtype=torch.float64, generator=g).to(dev)
+            for _ in range(2):
+                frob.gemm_f64(a, b, alpha=-1.0, beta=1.0, out=c)
+            sync()
+            print(f"gemm_f64 n={args.n}: done", flush=True)
+            return 0
         if args.once in ("frob_inv_hpd", "frob_inv_hpd_mixed"):
             # the 64 x n = 512 HPD workload (seed 2), or its first --batch matrices
             ms_ = W.hpd(512, batch=args.batch, seed=2)
@@ -885,8 +897,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "inversions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "arithmetic": "FP64 results; products of at least 256 in every dimension as exact BF16 digit products on "
-                      "the tensor cores (FP64-accurate), factorizations and the rest on the FP64 pipe",
+        "arithmetic": "FP64 results; products of at least 256 in every dimension, and smaller ones with M, N >= 128 "
+                      "and M N K >= 24 Mi, as exact BF16 digit products on the tensor cores (FP64-accurate); the "
+                      "triangular solves' diagonal blocks through their explicit inverses; panels and the rest on "
+                      "the FP64 pipe",
         "config": {"workload": WORKLOAD, "n": n, "seed": SEED, "s": S_ROT,
                    "construction": "A = I, B = Q blockdiag([[0,-s],[s,0]]) Q^T, Q Haar orthogonal (Sec. 3)",
                    "l2": "input (1.07 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
