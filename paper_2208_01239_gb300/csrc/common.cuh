@@ -185,6 +185,31 @@ template <typename F> inline void set_smem_attr(F* kernel, int bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// SMs that persistent kernels launched by this host thread leave free (a
+// panel factorization running beside them on another stream), and the grid
+// of such a kernel: at most one CTA per tile and per remaining SM.
+inline thread_local int t_sm_reserve = 0;
+inline unsigned persistent_grid(int64_t tiles) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int avail = sms - t_sm_reserve;
+  if (avail < 1) avail = 1;
+  return (unsigned)(tiles < avail ? tiles : avail);
+}
+
+// Scope of an SM reservation (restores the previous value).
+class SmReserve {
+ public:
+  explicit SmReserve(int n) : prev_(t_sm_reserve) { t_sm_reserve = n; }
+  ~SmReserve() { t_sm_reserve = prev_; }
+  SmReserve(const SmReserve&) = delete;
+  SmReserve& operator=(const SmReserve&) = delete;
+
+ private:
+  int prev_;
+};
+
 // Element-wise GEMM epilogues applied to W consecutive columns j0 .. j0 + W - 1
 // of row i (those below ncols): a functor with a row<W>() method (kRow) reads
 // every input of the W elements before it writes any, so that the loads are

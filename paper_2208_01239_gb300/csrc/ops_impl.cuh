@@ -652,17 +652,67 @@ template <typename T> inline const char* getrf_mc_name() {
   return s.c_str();
 }
 
+// The second stream of the LU's look-ahead (highest priority, so that a
+// panel waiting beside a product gets its SMs first) and its two events, per
+// host thread and created on first use; nullptr when the stream cannot be
+// made, the device changed, or `st` is being captured into a graph.
+struct PanelStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ready = nullptr;  // the next panel's columns are updated
+  cudaEvent_t done = nullptr;   // the next panel is factored
+  int dev = -1;
+  bool failed = false;
+  ~PanelStream() {
+    if (ready) cudaEventDestroy(ready);
+    if (done) cudaEventDestroy(done);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+inline thread_local PanelStream t_panel_stream;
+
+inline PanelStream* panel_stream(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  PanelStream& p = t_panel_stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (p.failed || (p.s && p.dev != dev)) return nullptr;
+  if (!p.s) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (cudaStreamCreateWithPriority(&p.s, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p.ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      p.failed = true;
+      return nullptr;
+    }
+    p.dev = dev;
+  }
+  return &p;
+}
+
 // Panels [kbeg, kend) of a right-looking LU with partial pivoting, in place:
 // each 32-wide panel is factored (by cooperating CTAs when `mc`), its row
 // exchanges are applied to every other column of the matrix, and U12 and the
 // trailing update reach the columns up to u_end (n: the whole matrix; a
 // recursive LU's block passes its right edge).
+//   Look-ahead (when the next panel takes the multi-CTA forms): the trailing
+// update first reaches the next panel's columns only; that panel is then
+// factored on the second stream while the rest of the update runs on `st`
+// with the panel's SMs (CL_MAX per matrix, at most half) left free by the
+// persistent product kernels, and the next exchange-and-U12 step waits for
+// both.  Neither waits on the other, so a panel that finds no room runs
+// after the product.  The two touch disjoint columns; the panel's row exchanges reach
+// the other columns only in that later step.
 template <typename T>
 inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info, int info_off, cudaStream_t st,
                          unsigned char* mcs, bool mc, int gcap, int kbeg, int kend, int u_end) {
   const int nb = panel_width<T>();
-  for (int k0 = kbeg; k0 < kend; k0 += nb) {
-    const int kb = std::min(nb, kend - k0);
+  auto panel = [&](int k0, int kb, cudaStream_t ps) {
     const int m = n - k0;
     const size_t bytes = (size_t)m * (kb + 1) * sizeof(T);
     const int staged = bytes <= PANEL_SMEM_MAX;
@@ -686,7 +736,7 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
       cfg.gridDim = dim3((unsigned)Gc, (unsigned)batch, 1);
       cfg.blockDim = dim3(MC_THREADS, 1, 1);
       cfg.dynamicSmemBytes = (size_t)Rc * (PANEL_MAX + 1) * sizeof(T);
-      cfg.stream = st;
+      cfg.stream = ps;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = (unsigned)Gc;
@@ -695,7 +745,7 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       cudaError_t le = cudaSuccess;
-      FROB_LAUNCH(getrf_cl_name<T>(), st,
+      FROB_LAUNCH(getrf_cl_name<T>(), ps,
                   le = cudaLaunchKernelEx(&cfg, getrf_panel_cl_kernel<T>, n, k0, kb, A, piv, info, info_off, Rc));
       if (le != cudaSuccess) {
         // refused (e.g. no room for the cluster): the cooperative-grid panel
@@ -712,18 +762,31 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
       const size_t smem = mc_smem<T>(R);
       int64_t bs = (int64_t)mc_scratch_per_matrix<T>();
       long long limit = 1ll << 31;  // about a second of SM clock
-      void* args[] = {(void*)&n, (void*)&k0, (void*)&kb, (void*)&A, (void*)&piv, (void*)&info, (void*)&info_off,
+      int k0v = k0, kbv = kb;
+      void* args[] = {(void*)&n, (void*)&k0v, (void*)&kbv, (void*)&A, (void*)&piv, (void*)&info, (void*)&info_off,
                       (void*)&mcs, (void*)&bs, (void*)&R, (void*)&limit};
-      FROB_LAUNCH(getrf_mc_name<T>(), st,
+      FROB_LAUNCH(getrf_mc_name<T>(), ps,
                   cudaLaunchCooperativeKernel((const void*)getrf_panel_mc_kernel<T>, dim3((unsigned)G, (unsigned)batch),
-                                              dim3(MC_THREADS), args, smem, st));
+                                              dim3(MC_THREADS), args, smem, ps));
     } else if (m <= PANEL_THREADS && sizeof(T) <= 8) {
-      FROB_LAUNCH(getrf_panel_name<T>(), st,
-                  getrf_panel_reg_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(n, k0, kb, A, piv, info, info_off));
+      FROB_LAUNCH(getrf_panel_name<T>(), ps,
+                  getrf_panel_reg_kernel<T><<<batch, PANEL_THREADS, 0, ps>>>(n, k0, kb, A, piv, info, info_off));
     } else {
-      FROB_LAUNCH(getrf_panel_name<T>(), st,
-                  getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, st>>>(n, k0, kb, A, piv, info,
+      FROB_LAUNCH(getrf_panel_name<T>(), ps,
+                  getrf_panel_kernel<T><<<batch, PANEL_THREADS, staged ? bytes : 0, ps>>>(n, k0, kb, A, piv, info,
                                                                                          info_off, staged));
+    }
+  };
+  // look-ahead only where the panels are multi-CTA and the stream is free to fork
+  PanelStream* la = (mc && kend - kbeg > nb) ? panel_stream(st) : nullptr;
+  bool pending = false;  // panel k0 was factored on la->s
+  for (int k0 = kbeg; k0 < kend; k0 += nb) {
+    const int kb = std::min(nb, kend - k0);
+    if (pending) {
+      cudaStreamWaitEvent(st, la->done, 0);
+      pending = false;
+    } else {
+      panel(k0, kb, st);
     }
     FROB_LAUNCH(laswp_name<T>(), st,
                 laswp_trsm_kernel<T><<<dim3((n + TB - 1) / TB, 1, batch), NTH, laswp_trsm_smem<T>(), st>>>(n, k0, kb, A,
@@ -733,8 +796,23 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
       MatB<const T> L21{A.p + (int64_t)r * A.ld + k0, A.ld, A.bs};
       MatB<const T> U12{A.p + (int64_t)k0 * A.ld + r, A.ld, A.bs};
       MatB<T> A22 = A.sub(r, r);
-      gemm_launch<T, OP_N, OP_N>(n - r, u_end - r, kb, batch, L21, U12,
-                                 axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false), 0, st);
+      const int nkb = std::min(nb, kend - r);  // the next panel's width (when r < kend)
+      if (la && r < kend && n - r > PANEL_THREADS && u_end - r > nkb) {
+        gemm_launch<T, OP_N, OP_N>(n - r, nkb, kb, batch, L21, U12, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
+                                   0, st);
+        cudaEventRecord(la->ready, st);
+        cudaStreamWaitEvent(la->s, la->ready, 0);
+        panel(r, nkb, la->s);
+        cudaEventRecord(la->done, la->s);
+        pending = true;
+        SmReserve keep(std::min(batch * CL_MAX, num_sms() / 2));
+        gemm_launch<T, OP_N, OP_N>(n - r, u_end - r - nkb, kb, batch, L21,
+                                   MatB<const T>{U12.p + nkb, U12.ld, U12.bs},
+                                   axpby<T>(A22.sub(0, nkb), neg_(one_v<T>()), one_v<T>(), false), 0, st);
+      } else {
+        gemm_launch<T, OP_N, OP_N>(n - r, u_end - r, kb, batch, L21, U12,
+                                   axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false), 0, st);
+      }
     }
   }
 }

@@ -575,12 +575,9 @@ bool prepare(int M, int N, int K, int batch, const double* A, int64_t lda, int64
 template <class Epi>
 inline cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const RArgs& a, Epi epi, cudaStream_t st) {
   set_smem_attr(ozr_gemm_kernel<Epi>, R_SMEM_BYTES);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (int64_t)((a.N + oz::BN - 1) / oz::BN) * ((a.M + tc::BM - 1) / tc::BM) * a.batch;
   if (tiles > INT32_MAX) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
+  const unsigned grid = persistent_grid(tiles);
   FROB_LAUNCH("ozr_gemm<f64 digits>", st,
               ozr_gemm_kernel<Epi><<<grid, oz::THREADS, R_SMEM_BYTES, st>>>(ma, mb, a, epi));
   return cudaGetLastError();

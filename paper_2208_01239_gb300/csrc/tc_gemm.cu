@@ -75,12 +75,9 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, i
   using S = TcSmem<BN, STAGES>;
   set_smem_attr(tc_gemm_kernel<KIND, BN, STAGES, Epi>, S::BYTES);
   // persistent: one CTA per SM (the shared memory admits no second), at most one per tile
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
   if (tiles > INT32_MAX) return cudaErrorInvalidValue;  // the kernel counts tiles in int
-  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
+  const unsigned grid = persistent_grid(tiles);
   FROB_LAUNCH(KIND == 0 ? "tc_gemm<bf16>" : "tc_gemm<tf32>", st,
               tc_gemm_kernel<KIND, BN, STAGES, Epi><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K, batch, epi,
                                                                                            err));

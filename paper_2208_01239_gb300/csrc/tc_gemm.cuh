@@ -370,12 +370,9 @@ inline cudaError_t tc3_launch(const CUtensorMap& ma, const CUtensorMap& mb, int 
   using S = TcSmem<BN, STAGES>;
   using E = TcEpiElem<Epi>;
   set_smem_attr(tc_gemm_kernel<1, BN, STAGES, E>, S::BYTES);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
   if (tiles > INT32_MAX) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(tiles < sms ? tiles : (sms > 0 ? sms : 1));
+  const unsigned grid = persistent_grid(tiles);
   const int K3 = (int)(3 * tc3_kp(K));
   FROB_LAUNCH("tc_gemm<3xtf32>", st,
               tc_gemm_kernel<1, BN, STAGES, E><<<grid, NUM_THREADS, S::BYTES, st>>>(ma, mb, M, N, K3, batch, E{epi},
