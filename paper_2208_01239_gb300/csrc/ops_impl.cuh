@@ -703,9 +703,8 @@ inline PanelStream* panel_stream(cudaStream_t st) {
 //   Look-ahead (when the next panel takes the multi-CTA forms): the trailing
 // update first reaches the next panel's columns only; that panel is then
 // factored on the second stream while the rest of the update runs on `st`
-// with the panel's SMs (CL_MAX per matrix, at most half) left free by the
-// persistent product kernels, and the next exchange-and-U12 step waits for
-// both.  Neither waits on the other, so a panel that finds no room runs
+// with the panel's CL_MAX SMs left free by the persistent product kernels,
+// and the next exchange-and-U12 step waits for both (single matrices only).  Neither waits on the other, so a panel that finds no room runs
 // after the product.  The two touch disjoint columns; the panel's row exchanges reach
 // the other columns only in that later step.
 template <typename T>
@@ -777,8 +776,10 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
                                                                                          info_off, staged));
     }
   };
-  // look-ahead only where the panels are multi-CTA and the stream is free to fork
-  PanelStream* la = (mc && kend - kbeg > nb) ? panel_stream(st) : nullptr;
+  // look-ahead only for a single matrix, whose multi-CTA panels leave most of
+  // the GPU idle (a batch's panels already spread over the SMs), and while the
+  // stream is free to fork
+  PanelStream* la = (mc && batch == 1 && kend - kbeg > nb) ? panel_stream(st) : nullptr;
   bool pending = false;  // panel k0 was factored on la->s
   for (int k0 = kbeg; k0 < kend; k0 += nb) {
     const int kb = std::min(nb, kend - k0);
@@ -805,7 +806,7 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
         panel(r, nkb, la->s);
         cudaEventRecord(la->done, la->s);
         pending = true;
-        SmReserve keep(std::min(batch * CL_MAX, num_sms() / 2));
+        SmReserve keep(CL_MAX);
         gemm_launch<T, OP_N, OP_N>(n - r, u_end - r - nkb, kb, batch, L21,
                                    MatB<const T>{U12.p + nkb, U12.ld, U12.bs},
                                    axpby<T>(A22.sub(0, nkb), neg_(one_v<T>()), one_v<T>(), false), 0, st);

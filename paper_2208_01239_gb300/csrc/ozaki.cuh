@@ -32,14 +32,15 @@
 // The groups are therefore issued in bands of four weights, {2 .. 5} and
 // {6 .. S + 1}; group g of the tile (per term and weight, in order) lives in
 // slot g mod 4, and its first MMA waits until the epilogue has drained group
-// g - 4.  Within a band the pairs go digit s of A outermost, so that each
-// group's last pair (its largest s) comes in order of weight and the groups
-// complete, and are drained, one after another while the tensor core works on
-// the rest of the band.
-// Operands: for each digit s of A
-// and each 128-wide K chunk, the 128 x 128 chunk of the digit slice stays in
-// shared memory (three chunk buffers) while the matching chunks of the B digit
-// slices t of the band stream through a 4-stage TMA ring (8 MMAs per stage).
+// g - 4.  Within a band the pairs go by pairs of A digits, smallest first, so
+// that each group's last pair (its largest s) comes in order of weight and
+// the groups complete, and are drained, one after another while the tensor
+// core works on the rest of the band.
+// Operands: for each pair of consecutive digits (s, s + 1) of A and each
+// 128-wide K chunk, the two 128 x 128 chunks of those digit slices stay in
+// shared memory (four chunk buffers) while the matching chunks of the B digit
+// slices t of the union of their runs stream once through a 3-stage TMA ring,
+// each stage feeding the pairs (s, t) and (s + 1, t) (8 MMAs each).
 //
 // Epilogue (8 warps; warp w reads TMEM lanes 32 (w mod 4) .. + 31 and one
 // 64-column half): each group is added, exactly, into a 64-bit fixed-point
@@ -71,11 +72,11 @@ constexpr int K_MAX = 512;    // largest inner dimension with exact FP32 accumul
 constexpr int CHUNK_KB = 2;                                // k-blocks per K chunk (128 K)
 constexpr int A_BOX_BYTES = tc::BM * KB * 2;               // 16 KB
 constexpr int A_CHUNK_BYTES = A_BOX_BYTES * CHUNK_KB;      // 32 KB
-constexpr int A_BUFS = 3;                                  // A chunk buffers
+constexpr int A_BUFS = 4;                                  // A chunk buffers (two digits in use, two loading)
 constexpr int A_RES_BYTES = A_BUFS * A_CHUNK_BYTES;
 constexpr int B_BOX_BYTES = BN * KB * 2;                   // 16 KB
 constexpr int B_STAGE_BYTES = B_BOX_BYTES * CHUNK_KB;      // 32 KB: 8 MMAs per stage
-constexpr int B_STAGES = 4;
+constexpr int B_STAGES = 3;
 constexpr int SLOTS = 4;                                   // 128-column TMEM accumulators
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;               // producer, MMA, epilogue warps
@@ -359,29 +360,32 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int ap = term, bp = term ? (T.part ^ 1) : T.part;
           for (int band = 0; band < num_bands(Su) && ok; ++band) {
             const int lo = band_lo(band), hi = band_hi(band, Su);
-            for (int s = 1; s <= Su && ok; ++s) {
-              const int tlo = lo - s > 1 ? lo - s : 1;
-              const int thi = hi - s < Su ? hi - s : Su;
-              if (tlo > thi) continue;
-              const int za = (ap * S + (s - 1)) * batch + T.b;
+            const int sa = lo - Su > 1 ? lo - Su : 1, sb = hi - 1 < Su ? hi - 1 : Su;  // digits with a run
+            for (int s1 = sa; s1 <= sb && ok; s1 += 2) {
+              const int s2 = s1 + 1 <= sb ? s1 + 1 : 0;
+              const int slead = s2 ? s2 : s1;
+              const int tlo = lo - slead > 1 ? lo - slead : 1;
+              const int thi = hi - s1 < Su ? hi - s1 : Su;
               for (int ch = 0; ch < nch && ok; ++ch) {
-                const int slot = ai % A_BUFS;
-                if (ai >= A_BUFS && !mbar_wait(&a_empty[slot], ((ai / A_BUFS) - 1) & 1)) { ok = false; break; }
-                mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
+                for (int q2 = 0; q2 < (s2 ? 2 : 1) && ok; ++q2) {
+                  const int s = q2 == 0 ? slead : s1;
+                  const int slot = ai % A_BUFS;
+                  if (ai >= A_BUFS && !mbar_wait(&a_empty[slot], ((ai / A_BUFS) - 1) & 1)) { ok = false; break; }
+                  mbar_arrive_expect_tx(&a_full[slot], (uint32_t)A_CHUNK_BYTES);
 #pragma unroll
-                for (int q = 0; q < CHUNK_KB; ++q)
-                  tma_load_3d(a_res + slot * A_CHUNK_BYTES + q * A_BOX_BYTES, &mapA, &a_full[slot],
-                              (ch * CHUNK_KB + q) * KB, T.m0, za);
-                ++ai;
+                  for (int q = 0; q < CHUNK_KB; ++q)
+                    tma_load_3d(a_res + slot * A_CHUNK_BYTES + q * A_BOX_BYTES, &mapA, &a_full[slot],
+                                (ch * CHUNK_KB + q) * KB, T.m0, (ap * S + (s - 1)) * batch + T.b);
+                  ++ai;
+                }
                 for (int t = tlo; t <= thi && ok; ++t) {
-                  const int zb = (bp * S + (t - 1)) * batch + T.b;
                   const int st = bi % B_STAGES;
                   if (bi >= B_STAGES && !mbar_wait(&b_empty[st], ((bi / B_STAGES) - 1) & 1)) { ok = false; break; }
                   mbar_arrive_expect_tx(&b_full[st], (uint32_t)B_STAGE_BYTES);
 #pragma unroll
                   for (int q = 0; q < CHUNK_KB; ++q)
                     tma_load_3d(b_ring + st * B_STAGE_BYTES + q * B_BOX_BYTES, &mapB, &b_full[st],
-                                (ch * CHUNK_KB + q) * KB, T.n0, zb);
+                                (ch * CHUNK_KB + q) * KB, T.n0, (bp * S + (t - 1)) * batch + T.b);
                   ++bi;
                 }
               }
@@ -409,52 +413,68 @@ __global__ void __launch_bounds__(THREADS, 1)
         const TileIdx T = tile_of(tile, nx, ny);
         if (args.skip && args.skip[T.b]) continue;
         for (int term = 0; term < 2 && ok; ++term) {
+          const int gt = g0 + term * Su;  // group of weight 2 of this term
           for (int band = 0; band < nb && ok; ++band) {
             const int lo = band_lo(band), hi = band_hi(band, Su);
+            const int sa = lo - Su > 1 ? lo - Su : 1, sb = hi - 1 < Su ? hi - 1 : Su;
             uint32_t started = 0;  // weights of this band whose accumulator has been initialised
-            for (int s = 1; s <= Su && ok; ++s) {
-              const int tlo = lo - s > 1 ? lo - s : 1;
-              const int thi = hi - s < Su ? hi - s : Su;
-              if (tlo > thi) continue;
+            for (int s1 = sa; s1 <= sb && ok; s1 += 2) {
+              const int s2 = s1 + 1 <= sb ? s1 + 1 : 0;
+              const int slead = s2 ? s2 : s1;
+              const int tlo = lo - slead > 1 ? lo - slead : 1;
+              const int thi = hi - s1 < Su ? hi - s1 : Su;
+              // runs: s1 over [t1lo, thi], s2 over [tlo, t2hi]
+              const int t1lo = lo - s1 > 1 ? lo - s1 : 1;
+              const int t2hi = s2 ? (hi - s2 < Su ? hi - s2 : Su) : 0;
               for (int ch = 0; ch < nch && ok; ++ch) {
-                const int aslot = ai % A_BUFS;
-                if (!mbar_wait(&a_full[aslot], (ai / A_BUFS) & 1)) { ok = false; break; }
+                int slot2 = 0;
+                if (s2) {
+                  slot2 = ai % A_BUFS;
+                  if (!mbar_wait(&a_full[slot2], (ai / A_BUFS) & 1)) { ok = false; break; }
+                  ++ai;
+                }
+                const int slot1 = ai % A_BUFS;
+                if (!mbar_wait(&a_full[slot1], (ai / A_BUFS) & 1)) { ok = false; break; }
                 ++ai;
                 tc_fence_after();
-                const uint32_t sa = smem_u32(a_res + aslot * A_CHUNK_BYTES);
                 for (int t = tlo; t <= thi && ok; ++t) {
-                  const int w = s + t;
-                  const int g = g0 + term * Su + (w - 2);
-                  if (!((started >> w) & 1u) && g >= SLOTS) {
-                    // first MMA of group g: slot g mod 4 must be drained of group g - 4
-                    if (!mbar_wait(&slot_empty[g % SLOTS], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
-                    tc_fence_after();
-                  }
                   const int st = bi % B_STAGES;
                   if (!mbar_wait(&b_full[st], (bi / B_STAGES) & 1)) { ok = false; break; }
                   tc_fence_after();
-                  const uint32_t sb = smem_u32(b_ring + st * B_STAGE_BYTES);
-                  const uint32_t dt = tmem + (uint32_t)((g % SLOTS) * BN);
-#pragma unroll
-                  for (int q = 0; q < CHUNK_KB; ++q)
-#pragma unroll
-                    for (int kk = 0; kk < KB / 16; ++kk) {
-                      const uint64_t ad = sw128_desc(sa + q * A_BOX_BYTES + kk * 32);
-                      const uint64_t bd = sw128_desc(sb + q * B_BOX_BYTES + kk * 32);
-                      mma<0>(dt, ad, bd, IDESC, ((started >> w) & 1u));
-                      started |= 1u << w;
+                  const uint32_t sbs = smem_u32(b_ring + st * B_STAGE_BYTES);
+                  for (int q2 = 0; q2 < 2; ++q2) {
+                    const int s = q2 == 0 ? s1 : s2;
+                    if (q2 == 0 ? (t < t1lo) : (s2 == 0 || t > t2hi)) continue;
+                    const int w = s + t;
+                    const int g = gt + (w - 2);
+                    if (!((started >> w) & 1u) && g >= SLOTS) {
+                      // first MMA of group g: slot g mod 4 must be drained of group g - 4
+                      if (!mbar_wait(&slot_empty[g % SLOTS], ((g / SLOTS) - 1) & 1)) { ok = false; break; }
+                      tc_fence_after();
                     }
+                    const uint32_t sas = smem_u32(a_res + (q2 == 0 ? slot1 : slot2) * A_CHUNK_BYTES);
+                    const uint32_t dt = tmem + (uint32_t)((g % SLOTS) * BN);
+#pragma unroll
+                    for (int q = 0; q < CHUNK_KB; ++q)
+#pragma unroll
+                      for (int kk = 0; kk < KB / 16; ++kk) {
+                        const uint64_t ad = sw128_desc(sas + q * A_BOX_BYTES + kk * 32);
+                        const uint64_t bd = sw128_desc(sbs + q * B_BOX_BYTES + kk * 32);
+                        mma<0>(dt, ad, bd, IDESC, ((started >> w) & 1u));
+                        started |= 1u << w;
+                      }
+                  }
                   mma_commit(&b_empty[st]);
                   ++bi;
+                  if (s2 && t == t2hi) mma_commit(&a_empty[slot2]);  // s2's last pair of this chunk
                 }
-                mma_commit(&a_empty[aslot]);  // chunk buffer free once these MMAs complete
+                mma_commit(&a_empty[slot1]);
               }
-              // groups whose last pair was digit s of A are complete
+              // groups whose last pair has A digit s1 or s2 are complete
               if (ok)
-                for (int t = tlo; t <= thi; ++t) {
-                  const int w = s + t;
+                for (int w = lo; w <= hi; ++w) {
                   const int slast = w - 1 < Su ? w - 1 : Su;
-                  if (s == slast) mma_commit(&slot_full[(g0 + term * Su + (w - 2)) % SLOTS]);
+                  if (slast == s1 || (s2 && slast == s2)) mma_commit(&slot_full[(gt + (w - 2)) % SLOTS]);
                 }
             }
           }
