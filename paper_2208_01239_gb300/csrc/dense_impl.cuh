@@ -298,6 +298,47 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, MatB<con
     }
 }
 
+// ------------------------------------------------------------------ narrow update
+// D[i][j] -= sum_k L[i][k] U[k][j] for N, K <= 32 (the next panel's columns in
+// the LU's look-ahead): 32 rows x N columns per CTA, 256 threads, each thread
+// 4 outputs of one column; L's rows and U staged in shared memory.  No
+// masked work (the 64 x 64 tiles of gemm_kernel would spend half their FMAs
+// on absent columns), and twice the CTAs.  grid (ceil(M / 32), 1, batch).
+template <typename T>
+__global__ void __launch_bounds__(256) update_narrow_kernel(int M, int N, int K, MatB<const T> L, MatB<const T> U,
+                                                            MatB<T> D) {
+  __shared__ T sl[32][33];
+  __shared__ T su[32][33];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.x * 32;
+  const int t = threadIdx.x;
+  const T* Lb = L.at(b);
+  const T* Ub = U.at(b);
+  for (int e = t; e < 32 * 32; e += 256) {
+    const int r = e >> 5, q = e & 31;
+    sl[r][q] = (i0 + r < M && q < K) ? Lb[(int64_t)(i0 + r) * L.ld + q] : zero_v<T>();
+    su[r][q] = (r < K && q < N) ? Ub[(int64_t)r * U.ld + q] : zero_v<T>();
+  }
+  __syncthreads();
+  const int j = t & 31, r0 = (t >> 5) * 4;  // column j, rows r0 .. r0 + 3
+  if (j >= N) return;
+  T acc[4] = {zero_v<T>(), zero_v<T>(), zero_v<T>(), zero_v<T>()};
+  for (int k = 0; k < K; ++k) {
+    const T u = su[k][j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mac(acc[q], sl[r0 + q][k], u);
+  }
+  T* Db = D.at(b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + r0 + q;
+    if (i < M) {
+      T* d = Db + (int64_t)i * D.ld + j;
+      *d = add_(*d, neg_(acc[q]));
+    }
+  }
+}
+
 // ------------------------------------------------------------------ mirror
 // Completes a symmetric (CONJ = false) or Hermitian (CONJ = true) matrix whose
 // 64 x 64 tiles on and below the diagonal are computed: A[i][j] = op(A[j][i])

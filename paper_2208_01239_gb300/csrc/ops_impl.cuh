@@ -799,8 +799,13 @@ inline void getrf_panels(int n, int batch, MatB<T> A, int* piv, frob_info* info,
       MatB<T> A22 = A.sub(r, r);
       const int nkb = std::min(nb, kend - r);  // the next panel's width (when r < kend)
       if (la && r < kend && n - r > PANEL_THREADS && u_end - r > nkb) {
-        gemm_launch<T, OP_N, OP_N>(n - r, nkb, kb, batch, L21, U12, axpby<T>(A22, neg_(one_v<T>()), one_v<T>(), false),
-                                   0, st);
+        // the next panel's columns (nkb, kb <= PANEL_MAX)
+        static_assert(PANEL_MAX <= 32, "update_narrow_kernel covers 32 columns and 32 of K");
+        static const std::string nname = std::string("update_narrow<") + type_tag<T>() + ">";
+        set_launch_flops(madd_flops<T>() * gemm_madds(n - r, nkb, kb, 0) * batch);
+        FROB_LAUNCH(nname.c_str(), st,
+                    update_narrow_kernel<T><<<dim3((unsigned)((n - r + 31) / 32), 1, (unsigned)batch), 256, 0, st>>>(
+                        n - r, nkb, kb, L21, U12, A22));
         cudaEventRecord(la->ready, st);
         cudaStreamWaitEvent(la->s, la->ready, 0);
         panel(r, nkb, la->s);
