@@ -372,8 +372,12 @@ frob_status aug_real_solve(int n, int nrhs, int batch, const void* M, int64_t ld
  * moduli; the rule of Sec. 5.3) or after kmax steps; the call returns when
  * every matrix of the batch has stopped, with X holding the last iterates and
  * steps[b] (device, int32 per matrix) the steps matrix b took.  The host
- * reads one 4-byte count after each step (a stream synchronisation), so the
- * call is not graph-capturable.  M and X as for frob_inv (complex128, or
+ * reads one 4-byte count after each step (a stream synchronisation) to stop
+ * early; while `stream` is being captured into a CUDA graph it reads
+ * nothing, the graph holds all kmax steps, and the matrices that met the
+ * rule stay unchanged in the later ones, so a replay gives the results and
+ * step counts of an uncaptured call (at the cost of the remaining steps'
+ * work; choose kmax accordingly).  M and X as for frob_inv (complex128, or
  * complex64 for FROB_FP32; X may equal M exactly, other overlap is an
  * error).  info[b] (device) is zero unless an inversion failed, in which case
  * it is that inversion's record and matrix b stopped there.  opts as for

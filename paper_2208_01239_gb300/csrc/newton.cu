@@ -199,6 +199,12 @@ frob_status newton_core(bool polar, int route, int n, int batch, MatB<C> X, cons
   void* inner_ws = take(inner_bytes);
 
   const int tb = 128, gb = (batch + tb - 1) / tb;
+  // Recorded into a graph, the host cannot read the running count: every
+  // step up to kmax is recorded, and the matrices that met the rule stay as
+  // they are (average_kernel and check_kernel skip them), so the results and
+  // step counts are those of an uncaptured call.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool captured = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
   FROB_LAUNCH("newton_init", st, init_kernel<<<gb, tb, 0, st>>>(batch, s, info, steps));
   const dim3 ag((unsigned)((n + TILE - 1) / TILE), (unsigned)((n + TILE - 1) / TILE), (unsigned)batch);
   const dim3 ab(TILE, ROWS);
@@ -216,6 +222,7 @@ frob_status newton_core(bool polar, int route, int n, int batch, MatB<C> X, cons
     else
       FROB_LAUNCH("newton_average<sign>", st, (average_kernel<C, false><<<ag, ab, 0, st>>>(n, X, yv, s)));
     FROB_LAUNCH("newton_check", st, check_kernel<<<gb, tb, 0, st>>>(batch, k, kmax, eps, s, steps));
+    if (captured) continue;
     int rem = 0;
     if (cudaMemcpyAsync(&rem, s.remaining, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -136,3 +136,30 @@ def test_polar_and_sylvester_fp32(F):
     a, b, c, y = W.sylvester_case(20, 12, seed=391)
     ry = F.sylvester(*(torch.from_numpy(t.astype(np.complex64)).cuda() for t in (a, b, c)), prec="fp32", eps=1e-4)
     assert _rel(ry.out.cpu().numpy().astype(np.complex128), y) <= 1e-3
+
+
+def test_sign_graph_capture(F):
+    """Recorded into a CUDA graph the driver cannot stop early (the host reads
+    no count): the graph holds all kmax steps and the matrices that met the
+    rule stay as they are, so each replay reproduces the uncaptured call's
+    iterates and step counts bit for bit."""
+    xs = np.stack([W.sign_case(48, seed=320 + b, re_lo=0.05 + 0.4 * b, re_hi=0.5 + 0.6 * b)[0] for b in range(3)])
+    m = torch.from_numpy(xs).cuda()
+    eager = F.sign(m, eps=1e-10, kmax=40)
+    want, want_steps = eager.out.cpu().numpy(), eager.steps()
+    assert len(set(want_steps.tolist())) > 1 and max(want_steps) < 40
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up on the capture stream, outside the capture
+        F.sign(m, eps=1e-10, kmax=40, check=False)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r = F.sign(m, eps=1e-10, kmax=40, check=False)
+    for _ in range(2):
+        r.out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(r.steps(), want_steps)
+        assert np.array_equal(r.out.cpu().numpy(), want)
