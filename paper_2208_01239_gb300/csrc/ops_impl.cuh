@@ -189,9 +189,10 @@ struct TcScratch {
   int* err = nullptr;
 };
 inline thread_local TcScratch t_tc;
-// The same for the FP64 drivers: FP64 products of at least ozr::MIN_MNK in
-// every dimension run as exact digit products on the BF16 tensor cores
-// (ozr.cuh) while an OzScope is open.
+// The same for the FP64 drivers: FP64 products of a digit shape
+// (ozr::digit_shape: at least ozr::MIN_MNK in every dimension, or thinner
+// ones large enough to beat the FP64 pipe) run as exact digit products on
+// the BF16 tensor cores (ozr.cuh) while an OzScope is open.
 inline thread_local TcScratch t_oz;
 inline TcScratch& tc_slot() { return t_tc; }
 inline TcScratch& oz_slot() { return t_oz; }

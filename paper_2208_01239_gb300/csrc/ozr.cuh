@@ -40,10 +40,12 @@
 // of the correctly rounded product, against ten or more for FP64 dot products.
 //
 // Kernel: as oz_cgemm_kernel (persistent CTAs, one per SM; a producer warp
-// with a TMA ring of B digit stages and three resident A digit chunks, an MMA
-// warp, eight epilogue warps; 128 x 128 tiles; four 128-column TMEM slots,
-// group g in slot g mod 4; weights in bands of four), with one real term per
-// tile and an outer loop over the 512-wide K chunks.  Every mbarrier wait is
+// keeping two consecutive A digits resident per 128-wide K slice in four A
+// chunk buffers while the B digit stages of the union of their runs stream
+// once through a 3-stage TMA ring, an MMA warp, eight epilogue warps;
+// 128 x 128 tiles; four 128-column TMEM slots, group g in slot g mod 4;
+// weights in bands of four), with one real term per tile and an outer loop
+// over the 512-wide K chunks.  Every mbarrier wait is
 // bounded (tc::mbar_wait); a wait that gives up sets the caller's flag to
 // FROB_ERR_TIMEOUT, the producer lets its copies land and the CTA returns.
 #pragma once
